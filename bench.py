@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark: spin-flip attempts per second of population annealing on a
+G63-shaped Max-Cut instance (N = 7000, M = 41,459 unweighted random edges),
+R = 16384 replicas, beta linear 0.1 -> 4.0 in K = 1000 steps, 10 sweeps per
+step, Houdayer non-local moves every 50 steps (synthetic seeded graph).
+
+One benchmark step = one whole anneal (all temperature steps: resampling,
+sweeps, best tracking, non-local moves), N R S K = 1.147e12 attempts.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank anneals its own
+instance (seed + rank): independent problems, no data-path collective, weak
+scaling; the harness barrier and the max-over-ranks time use torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin-flip attempts/s at N=7000 R=16384 + batched/served vs plain, bit-exact"
+UNIT = "attempts/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SMS = 152
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--config", default="g63like")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="approximate CPU time of the oracle sample")
+    return p.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# --------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows)}
+
+
+# ------------------------------------------------------ reference (oracle) ---
+def cpu_oracle_sample(cfg_name: str, seconds: float):
+    """Time the oracle on a bounded sample of the benchmark workload: the same
+    graph and schedule, a few replicas, the first temperature steps."""
+    import oracle
+    from paper_2510_21105_gb300 import workloads as wl
+
+    c = wl.CONFIGS[cfg_name]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    R = 16
+    # calibrate: 2 steps, then scale the step count to the time budget
+    t0 = time.perf_counter()
+    oracle.anneal(g.rp, g.col, g.w, betas[:2], R=R, S=c["S"], seed=c["seed"])
+    per_step = (time.perf_counter() - t0) / 2
+    K = int(max(2, min(c["K"], seconds / max(per_step, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.anneal(g.rp, g.col, g.w, betas[:K], R=R, S=c["S"], seed=c["seed"],
+                  nlm_period=c["nlm_period"])
+    dt = time.perf_counter() - t0
+    attempts = g.n * R * c["S"] * K
+    return {"value": attempts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{cfg_name} graph, R={R}, first {K} of {c['K']} steps x {c['S']} sweeps "
+                      f"({attempts:.3g} attempts, {dt:.1f} s, single thread)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_2510_21105_gb300 import workloads as wl
+
+    c = wl.CONFIGS[args.config]
+    samples = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(args.config, min(args.cpu_seconds, 3.0))
+    for _ in range(args.steps):
+        samples.append(cpu_oracle_sample(args.config, args.cpu_seconds))
+    v = statistics.median(s["value"] for s in samples)
+    ms = 1000.0 * (wl.CONFIGS[args.config]["graph"]().n * c["R"] * c["S"] * c["K"]) / v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{args.config}: N=7000 M=41459 R={c['R']} K={c['K']} S={c['S']} "
+                                   f"nlm_period={c['nlm_period']}", "l2": "n/a (CPU)"},
+            "cpu_baseline": {**samples[-1], "value": v},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ ours ---
+def sweep_roofline(stats, attempts_per_launch, peaks, clocks):
+    """Roofline of the sweep kernel (dominant kernel): integer-ALU bound. The
+    algorithmic integer work per attempt is the Philox share fixed by the
+    bit-exact contract plus the Metropolis decision."""
+    ops_per_attempt = 20.0
+    lanes_per_sm = 64.0
+    launches = max(stats["sweep_launches"], 1)
+    t = stats["sweep_ms"] / launches / 1e3
+    if t <= 0:
+        return None
+    achieved = attempts_per_launch * ops_per_attempt / t / 1e12
+    peak = SMS * lanes_per_sm * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "k_sweep", "avg_launch_ms": t * 1e3,
+            "attempts_per_s_in_kernel": attempts_per_launch / t}
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+
+    from paper_2510_21105_gb300 import binding as B
+    from paper_2510_21105_gb300 import build as build_mod
+    from paper_2510_21105_gb300 import workloads as wl
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build_mod.build()
+    if dist:
+        dist.barrier()
+    B.lib()
+    c = wl.CONFIGS[args.config]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    R, S, K = c["R"], c["S"], c["K"]
+    seed = c["seed"] + rank
+    stream = torch.cuda.current_stream()
+    sh = B.C.c_void_p(stream.cuda_stream)
+    attempts = g.n * R * S * K
+
+    ann = B.Annealer.from_graph(g)
+
+    def one(time_kernels=0):
+        ann.anneal(betas, R, S, seed, nlm_period=c["nlm_period"], stream=sh,
+                   time_kernels=time_kernels)
+
+    for _ in range(args.warmup):
+        one()
+    peaks, peaks_src = load_peaks()
+    # timed region: device-resident inputs, K anneals
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stats_acc = {"sweep_ms": 0.0, "sweep_launches": 0, "kernel_launches": 0}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            one(time_kernels=1)
+            st = ann.stats()
+            for key in stats_acc:
+                stats_acc[key] += st[key]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t_best = st["t_best_ms"]
+    cut, _, best_step, _ = ann.best()
+    ms_max = ms
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_max = float(tt.item())
+    value = world * attempts / (ms_max / 1e3)
+    clocks = clk.summary()
+    roof = sweep_roofline(stats_acc, g.n * R * S, peaks, clocks)
+    ann.close()
+
+    # end to end through the C-ABI with host buffers (pinned), copies inside the region
+    e2e = None
+    if not args.no_e2e:
+        rp = torch.from_numpy(g.rp_u32).pin_memory()
+        col = torch.from_numpy(g.col_u16.view(np.int16)).pin_memory()
+        hb = torch.from_numpy(betas).pin_memory()
+        cfg = torch.empty(g.n, dtype=torch.int8).pin_memory()
+        lib = B.lib()
+        times, h2d, d2h = [], 0, 0
+        for it in range(args.steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx = B.C.c_void_p()
+            rc = lib.pa_create(B.C.byref(ctx), g.n, rp.data_ptr(), col.data_ptr(), None)
+            assert rc == 0, rc
+            o = B.pa_default_opts(nlm_period=c["nlm_period"], stream=sh)
+            rc = lib.pa_anneal(ctx, hb.data_ptr(), K, R, S, seed, B.C.byref(o))
+            assert rc == 0, rc
+            cutv = B.C.c_int64()
+            rc = lib.pa_best(ctx, B.C.byref(cutv), cfg.data_ptr(), None, None)
+            assert rc == 0, rc
+            st2 = B.pa_stats(ctx)
+            lib.pa_destroy(ctx)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if it > 0:   # the first call pays the context's one-time set-up
+                times.append(dt)
+                h2d, d2h = st2["h2d_bytes"], st2["d2h_bytes"]
+        e2e_s = max(statistics.median(times), 1e-9)
+        if dist:
+            tt = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
+
+    if rank != 0:
+        return 0
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        cpu = cpu_oracle_sample(args.config, args.cpu_seconds)
+    if roof is not None:
+        roof["peak_source"] = f"derived: {SMS} SMs x 64 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8/int16 spins+fields, fp64 weights",
+            "data": "synthetic",
+            "config": {"workload": f"{args.config}: G63-shaped N={g.n} M={g.m} R={R} K={K} S={S} "
+                                   f"beta {c['beta'][0]}->{c['beta'][1]} nlm_period={c['nlm_period']}",
+                       "l2": "inputs larger than L2 (population 688 MB per buffer pair)",
+                       "seed": c["seed"]},
+            "best_cut": int(cut), "best_step": int(best_step), "time_to_best_ms": t_best,
+            "e2e": e2e, "gpu_launches": stats_acc["kernel_launches"],
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "peaks": peaks_src}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+
+        backend = "nccl" if (torch.cuda.is_available() and args.impl == "ours") else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group(backend)
+        dist = tdist
+    try:
+        if args.impl == "reference":
+            return run_reference(args, rank, world)
+        return run_ours(args, rank, world, dist)
+    finally:
+        if dist:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,232 @@
+/*
+ * pa.h -- C ABI of libpa.so: Population Annealing Monte Carlo (PAMC) for
+ * Max-Cut on one GB300 GPU (hand-written CUDA for sm_103a).
+ *
+ * Method (arXiv 2510.21105):
+ *   Eq. 1   Max-Cut: maximise 1/2 sum_{i<j} w_ij (1 - x_i x_j), x in {-1,+1}^N.
+ *   Sec. 2  Equivalently minimise the Ising energy with couplings -w_ij:
+ *           E(x) = sum_{i<j} w_ij x_i x_j, and cut(x) = (W - E(x)) / 2 with
+ *           W = sum_{i<j} w_ij.
+ *   Sec. 3  The solver is PAMC (a population of replicas annealed in inverse
+ *           temperature beta with Metropolis sweeps and Boltzmann
+ *           resampling between temperatures), with adaptive control of
+ *           stochasticity and periodic non-local moves, on one GPU. The
+ *           paper defines these steps no further; the library implements the
+ *           readings documented per entry point below, and every random
+ *           decision is a counter-based Philox4x32-10 word keyed by the seed,
+ *           so results are bit-identical run to run and independent of launch
+ *           configuration.
+ *
+ * Conventions (all entry points):
+ *   - Return 0 (PA_OK) on success or a negative PA_E* code. pa_strerror()
+ *     names a code; pa_last_error() gives the detail of the last failure on a
+ *     context. A failed call leaves previously returned results unchanged.
+ *   - Host pointers are read or written synchronously and never retained:
+ *     the caller owns every array it passes. Device memory is owned by the
+ *     context and released by pa_destroy().
+ *   - Vertices are numbered 0..n-1 (the paper numbers them 1..N).
+ *   - The graph is CSR with every undirected edge stored in both rows:
+ *     row_ptr[n+1] (uint32, row_ptr[0] = 0), col[row_ptr[n]] (uint16
+ *     neighbour indices, so n <= 65536), w[row_ptr[n]] (int8 weights +1/-1,
+ *     or NULL for all +1). The two copies of an edge must carry the same
+ *     weight.
+ *   - One context drives one GPU: the device current at pa_create().
+ */
+#ifndef PA_H
+#define PA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PA_OK 0
+#define PA_EINVAL (-1)   /* invalid argument (graph, schedule, sizes, options) */
+#define PA_ENOMEM (-2)   /* device or host allocation failed */
+#define PA_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
+#define PA_ETIMEOUT (-4) /* a bounded device-side wait expired */
+#define PA_EBUSY (-5)    /* the server is at its admission limit */
+#define PA_ESTATE (-6)   /* call out of order (e.g. pa_best before any sweep) */
+
+typedef struct pa_ctx pa_ctx;
+
+/* Sweep kernel variants. */
+#define PA_VARIANT_I8 0   /* int8 spins + int16/int8 local fields in shared memory */
+#define PA_VARIANT_MSC 1  /* multi-spin coded: 32 replicas per 32-bit word */
+#define PA_VARIANT_AUTO 2 /* chosen per graph by the built-in tuning table */
+
+typedef struct {
+    int32_t variant;          /* PA_VARIANT_*; default PA_VARIANT_I8 */
+    int32_t field_bits;       /* I8 variant: width of local fields in shared
+                                 memory, 16 (default) or 8 (needs max degree
+                                 <= 127) */
+    int32_t nlm_period;       /* non-local (Houdayer) move after the sweeps of
+                                 step k when k > 0 and k % nlm_period == 0;
+                                 0 = off (default) */
+    int32_t adaptive;         /* 0 = schedule from betas[] (default);
+                                 1 = ESS-adaptive temperature steps */
+    double rho;               /* adaptive: target ESS / R, in (0, 1] */
+    int32_t adapt_J;          /* adaptive: finest level J (0..20) */
+    double adapt_dbeta_max;   /* adaptive: coarsest step dbeta_max > 0 */
+    double beta_max;          /* adaptive: final inverse temperature */
+    int32_t replicas_per_cta; /* I8 variant: 4 or 8; 0 = auto */
+    int32_t threads_per_cta;  /* 128..1024, multiple of 32; 0 = auto */
+    void *stream;             /* cudaStream_t for every launch and copy;
+                                 NULL = the legacy default stream */
+    int32_t record_counts;    /* 1 = keep per-step copy counts (steps x R) */
+    int32_t time_kernels;     /* 1 = time every sweep launch with CUDA events */
+} pa_anneal_opts;
+
+typedef struct {
+    int64_t attempts;         /* spin-flip attempts: n * R * sweeps * steps run */
+    int64_t accepts;          /* accepted flips in all sweeps */
+    int32_t steps_run;        /* temperature steps completed */
+    int32_t n_colours;        /* colours of the greedy colouring */
+    int32_t max_degree;
+    int32_t kernel_launches;  /* library kernels launched by the anneal calls */
+    int32_t sweep_launches;   /* of which sweep kernels */
+    int32_t variant;          /* sweep variant actually used */
+    double anneal_ms;         /* device time of the anneal calls (CUDA events) */
+    double sweep_ms;          /* summed sweep-kernel time (time_kernels = 1) */
+    double t_best_ms;         /* device time from the first step to the end of
+                                 the step that recorded the final best */
+    int64_t total_weight;     /* W = sum over undirected edges of w_ij */
+    int64_t h2d_bytes;        /* host-to-device bytes copied by this context */
+    int64_t d2h_bytes;        /* device-to-host bytes copied by this context */
+} pa_stats_t;
+
+/* Per-step records; each pointer may be NULL, arrays hold steps_run entries
+ * (sweep_emin: steps_run * sweeps, counts: steps_run * R). */
+typedef struct {
+    double *beta;             /* beta_k used by the sweeps of step k */
+    int32_t *emin;            /* minimum energy entering the resampling of step k */
+    double *A;                /* FP64 weight sum A_k = sum_r exp(-dbeta (E_r - E_min)) */
+    uint64_t *T;              /* integer weight total of the resampling */
+    uint32_t *o;              /* systematic-resampling offset word */
+    int64_t *accepts;         /* accepted flips in the sweeps of step k */
+    double *lnZ;              /* free-energy estimate ln Z(beta_k) */
+    int32_t *sweep_emin;      /* minimum energy over replicas after each sweep */
+    int32_t *nlm_pairs;       /* non-local moves performed (pairs with D != {}) */
+    int64_t *nlm_flips;       /* spins flipped per replica by those moves */
+    int32_t *jsel;            /* adaptive: chosen level j (-1 otherwise) */
+    int32_t *counts;          /* copy counts n_r (record_counts = 1) */
+} pa_step_arrays;
+
+/* Fill *o with the defaults listed above. */
+void pa_default_opts(pa_anneal_opts *o);
+
+/* Create a context for one Max-Cut instance (Eq. 1; Ising form of Sec. 2).
+ * Validates the CSR (n in 1..65536, row_ptr monotone, no self loops, no
+ * duplicate neighbours, symmetric with equal weights, w in {+1,-1}), computes
+ * the first-fit greedy colouring in vertex order (colour classes are the
+ * parallel update sets of a sweep), renumbers vertices by colour, and copies
+ * the graph to the current device. Errors: PA_EINVAL, PA_ENOMEM, PA_ECUDA;
+ * *out is set only on success. */
+int pa_create(pa_ctx **out, int32_t n, const uint32_t *row_ptr, const uint16_t *col,
+              const int8_t *w);
+
+/* Release the context and all its device memory (NULL is allowed). Waits
+ * for the context's work to finish. */
+void pa_destroy(pa_ctx *ctx);
+
+/* Run a whole anneal: pa_anneal_begin() then pa_anneal_run(ctx, K), then
+ * wait for completion. Sec. 3 (PAMC). Schedule: step k = 0..K-1 resamples
+ * the population from beta_{k-1} to beta_k (beta_{-1} = 0, the initial i.i.d.
+ * uniform population being exact at beta = 0), runs `sweeps` Metropolis
+ * sweeps at beta_k (colour classes in order; a flip with energy change
+ * dE = 2m is accepted iff m <= 0 or u < floor(2^32 exp(-2 beta_k m)), u the
+ * Philox word of (spin, slot, step, sweep)), records the best energy after
+ * every sweep, and applies the non-local move when due.
+ * betas: host array of K finite, non-negative, non-decreasing doubles
+ * (ignored, may be NULL, when opts->adaptive = 1; K is then the maximum
+ * number of steps). R: replicas, 1..65536. sweeps >= 0. opts: NULL =
+ * defaults. Errors: PA_EINVAL, PA_ENOMEM, PA_ECUDA. */
+int pa_anneal(pa_ctx *ctx, const double *betas, int32_t K, int32_t R, int32_t sweeps,
+              uint64_t seed, const pa_anneal_opts *opts);
+
+/* Allocate the population (R replicas, device resident), build the per-step
+ * acceptance tables and resampling power tables on the host, and initialise
+ * spins, local fields and energies on the device. No temperature step runs.
+ * Arguments and errors as pa_anneal(). */
+int pa_anneal_begin(pa_ctx *ctx, const double *betas, int32_t K, int32_t R, int32_t sweeps,
+                    uint64_t seed, const pa_anneal_opts *opts);
+
+/* Enqueue temperature steps [steps done, k_end) on the context's stream and
+ * return without waiting (pa_sync waits). k_end is clamped to K. In adaptive
+ * mode the steps after beta_max is reached are skipped on the device.
+ * Errors: PA_ESTATE (no pa_anneal_begin), PA_EINVAL, PA_ECUDA. */
+int pa_anneal_run(pa_ctx *ctx, int32_t k_end);
+
+/* Wait for the context's stream; report a pending kernel error. */
+int pa_sync(pa_ctx *ctx);
+
+/* Best cut found so far (Sec. 3 reports one best cut and its configuration):
+ * the lexicographic minimum of (energy, step, sweep, slot) over all sweep
+ * ends. cut = (W - E*) / 2. config (may be NULL): host int8[n] of +1/-1 in
+ * vertex order. step, sweep (may be NULL): where it was first recorded.
+ * Waits for pending work. Errors: PA_ESTATE if no sweep has run. */
+int pa_best(pa_ctx *ctx, int64_t *cut, int8_t *config, int32_t *step, int32_t *sweep);
+
+/* As pa_best, also returning the best energy and the slot that held it. */
+int pa_best_record(pa_ctx *ctx, int32_t *energy, int32_t *step, int32_t *sweep, int32_t *slot);
+
+/* Copy the current population to the host: spins int8[R][n] (+1/-1, vertex
+ * order; may be NULL) and energies int32[R] (may be NULL). Waits for pending
+ * work. Errors: PA_ESTATE before pa_anneal_begin. */
+int pa_get_state(pa_ctx *ctx, int8_t *spins, int32_t *energies);
+
+/* Replace the population by host spins int8[R][n] (+1/-1, vertex order) and
+ * mark `steps_done` steps as completed (resume / replay). Fields and energies
+ * are recomputed on the device. Errors: PA_ESTATE, PA_EINVAL. */
+int pa_set_state(pa_ctx *ctx, const int8_t *spins, int32_t steps_done);
+
+/* Checkpoint: write the anneal parameters, the population and the best
+ * record to `path`; pa_load restores them into a context created for the
+ * same graph (resume is bit-exact because all randomness is counter based).
+ * Errors: PA_ESTATE, PA_EINVAL (unreadable file or different graph). */
+int pa_save(pa_ctx *ctx, const char *path);
+int pa_load(pa_ctx *ctx, const char *path);
+
+/* Parameters of the current anneal (any pointer may be NULL); useful after
+ * pa_load. Errors: PA_ESTATE before pa_anneal_begin. */
+int pa_run_info(pa_ctx *ctx, int32_t *R, int32_t *K, int32_t *sweeps, int32_t *steps_done);
+
+/* Totals and timings of the anneal (waits for pending work). */
+int pa_stats(pa_ctx *ctx, pa_stats_t *out);
+
+/* Per-step records (waits for pending work). */
+int pa_step_stats(pa_ctx *ctx, pa_step_arrays *out);
+
+/* Host-side copies of the tables the device uses for step k: the 32-bit
+ * acceptance thresholds T[0..max_degree] and the 32 squarings q^(2^b) of
+ * q = exp(-(beta_k - beta_{k-1})) used for the resampling weights. Either
+ * pointer may be NULL. Errors: PA_ESTATE, PA_EINVAL. */
+int pa_tables(pa_ctx *ctx, int32_t k, uint32_t *accept, double *qpow);
+
+/* Colouring and renumbering chosen by pa_create: colour[n] per vertex,
+ * position[n] of each vertex in the colour-sorted order (either may be
+ * NULL). Returns the number of colours, or a negative error. */
+int pa_colouring(pa_ctx *ctx, int32_t *colour, int32_t *position);
+
+/* Device allocator hook (e.g. a framework's caching allocator). alloc
+ * returns device memory of at least `bytes` bytes aligned to 256 bytes or
+ * NULL; free releases it. Applies to allocations made after the call; NULL
+ * functions restore cudaMalloc / cudaFree. Not thread safe against
+ * concurrent allocations. */
+typedef void *(*pa_alloc_fn)(size_t bytes, void *user);
+typedef void (*pa_free_fn)(void *ptr, void *user);
+void pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_fn, void *user);
+
+/* Text of an error code, and the detail of the last error on ctx. */
+const char *pa_strerror(int code);
+const char *pa_last_error(const pa_ctx *ctx);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int32_t pa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PA_H */

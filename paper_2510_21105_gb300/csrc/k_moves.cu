@@ -1,0 +1,338 @@
+// k_moves.cu -- Houdayer non-local moves and ESS-adaptive temperature steps
+// (Sec. 3 of arXiv 2510.21105 names both without defining them; the rules
+// implemented here are the library's readings, stated in pa_moves.cuh).
+#include "pa_moves.cuh"
+
+namespace pa {
+namespace {
+
+// ------------------------------------------------------------ non-local ---
+__global__ void k_nlm_keys(NlmArgs a, uint32_t *keys) {
+    if (a.active && !a.active[a.k]) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.R) return;
+    const uint4 u = philox10(make_uint4((uint32_t)r >> 2, 0u, (uint32_t)a.k, TAG_NONLOCAL), a.key0, a.key1);
+    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+    keys[r] = uu[r & 3];
+}
+
+// Rank of (key_r, r) among all slots by direct counting; order[rank] = r.
+__global__ void k_nlm_rank(NlmArgs a, const uint32_t *keys, int32_t *order) {
+    if (a.active && !a.active[a.k]) return;
+    __shared__ uint32_t tile[2048];
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t kr = r < a.R ? keys[r] : 0u;
+    int rank = 0;
+    for (int t0 = 0; t0 < a.R; t0 += 2048) {
+        const int tn = min(2048, a.R - t0);
+        __syncthreads();
+        for (int i = threadIdx.x; i < tn; i += blockDim.x) tile[i] = keys[t0 + i];
+        __syncthreads();
+        if (r < a.R)
+            for (int i = 0; i < tn; ++i) {
+                const uint32_t ks = tile[i];
+                rank += (ks < kr) || (ks == kr && t0 + i < r);
+            }
+    }
+    if (r < a.R) order[rank] = r;
+}
+
+__global__ void k_nlm_pair(NlmArgs a, const int32_t *order) {
+    if (a.active && !a.active[a.k]) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int np = a.g.np, n = a.g.n;
+    int8_t *xa = reinterpret_cast<int8_t *>(sm);
+    int8_t *xb = xa + np;
+    uint32_t *vis = reinterpret_cast<uint32_t *>(xb + np);
+    const int nw = (np + 31) >> 5;
+    uint16_t *fr0 = reinterpret_cast<uint16_t *>(vis + nw);
+    uint16_t *fr1 = fr0 + np;
+    __shared__ int sh_cnt[1024];
+    __shared__ int sh_nd, sh_seed, sh_next;
+    __shared__ long long sh_E[2][32];
+    const int tid = threadIdx.x, NT = blockDim.x;
+    const int m = blockIdx.x;
+    const int sa = order[2 * m], sb = order[2 * m + 1];
+    {
+        const uint4 *ga = reinterpret_cast<const uint4 *>(a.spins + (size_t)sa * np);
+        const uint4 *gb = reinterpret_cast<const uint4 *>(a.spins + (size_t)sb * np);
+        uint4 *la = reinterpret_cast<uint4 *>(xa), *lb = reinterpret_cast<uint4 *>(xb);
+        for (int i = tid; i < (np >> 4); i += NT) {
+            la[i] = ga[i];
+            lb[i] = gb[i];
+        }
+        for (int i = tid; i < nw; i += NT) vis[i] = 0u;
+    }
+    __syncthreads();
+    // |D| and the seed: the target-th element of D in ascending vertex order.
+    const int per = (n + NT - 1) / NT;
+    const int i0 = tid * per, i1 = min(n, i0 + per);
+    int cnt = 0;
+    for (int i = i0; i < i1; ++i) {
+        const int p = a.pos[i];
+        cnt += xa[p] != xb[p];
+    }
+    sh_cnt[tid] = cnt;
+    __syncthreads();
+    if (tid == 0) {
+        int s = 0;
+        for (int t = 0; t < NT; ++t) {
+            const int c = sh_cnt[t];
+            sh_cnt[t] = s;
+            s += c;
+        }
+        sh_nd = s;
+        sh_seed = -1;
+    }
+    __syncthreads();
+    const int nd = sh_nd;
+    if (nd == 0) return;
+    const uint4 u = philox10(make_uint4((uint32_t)m >> 2, 1u, (uint32_t)a.k, TAG_NONLOCAL), a.key0, a.key1);
+    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+    const int target = (int)(uu[m & 3] % (uint32_t)nd);
+    const int pre = sh_cnt[tid];
+    if (target >= pre && target < pre + cnt) {
+        int c = pre;
+        for (int i = i0; i < i1; ++i) {
+            const int p = a.pos[i];
+            if (xa[p] != xb[p]) {
+                if (c == target) { sh_seed = p; break; }
+                ++c;
+            }
+        }
+    }
+    __syncthreads();
+    if (sh_seed < 0) return;   // unreachable when nd > 0; keeps every index in range
+    // Breadth-first search of the seed's component in the graph induced on D.
+    if (tid == 0) {
+        const int s = sh_seed;
+        vis[s >> 5] |= 1u << (s & 31);
+        fr0[0] = (uint16_t)s;
+    }
+    int fsize = 1, csize = 1;
+    uint16_t *cur = fr0, *nxt = fr1;
+    __syncthreads();
+    while (fsize > 0) {
+        if (tid == 0) sh_next = 0;
+        __syncthreads();
+        for (int f = tid; f < fsize; f += NT) {
+            const int p = cur[f];
+            const uint32_t e1 = a.g.rp[p + 1];
+            for (uint32_t e = a.g.rp[p]; e < e1; ++e) {
+                const int j = a.g.col[e];
+                if (xa[j] != xb[j]) {
+                    const uint32_t bit = 1u << (j & 31);
+                    if (!(atomicOr(&vis[j >> 5], bit) & bit)) nxt[atomicAdd(&sh_next, 1)] = (uint16_t)j;
+                }
+            }
+        }
+        __syncthreads();
+        fsize = sh_next;
+        csize += fsize;
+        uint16_t *t = cur;
+        cur = nxt;
+        nxt = t;
+        __syncthreads();
+    }
+    // Flip both replicas on the cluster.
+    for (int p = tid; p < n; p += NT)
+        if ((vis[p >> 5] >> (p & 31)) & 1u) {
+            xa[p] = (int8_t)-xa[p];
+            xb[p] = (int8_t)-xb[p];
+        }
+    __syncthreads();
+    {
+        uint4 *ga = reinterpret_cast<uint4 *>(a.spins + (size_t)sa * np);
+        uint4 *gb = reinterpret_cast<uint4 *>(a.spins + (size_t)sb * np);
+        const uint4 *la = reinterpret_cast<const uint4 *>(xa), *lb = reinterpret_cast<const uint4 *>(xb);
+        for (int i = tid; i < (np >> 4); i += NT) {
+            ga[i] = la[i];
+            gb[i] = lb[i];
+        }
+    }
+    // Fields and energies of both replicas, recomputed.
+    long long Ea = 0, Eb = 0;
+    int16_t *fa = a.fields + (size_t)sa * np, *fb = a.fields + (size_t)sb * np;
+    for (int p = tid; p < np; p += NT) {
+        int ha = 0, hb = 0;
+        if (p < n) {
+            const uint32_t e1 = a.g.rp[p + 1];
+            for (uint32_t e = a.g.rp[p]; e < e1; ++e) {
+                const int j = a.g.col[e];
+                const int w = a.g.wt ? (int)a.g.wt[e] : 1;
+                ha += w * xa[j];
+                hb += w * xb[j];
+            }
+            Ea += (long long)xa[p] * ha;
+            Eb += (long long)xb[p] * hb;
+        }
+        fa[p] = (int16_t)ha;
+        fb[p] = (int16_t)hb;
+    }
+    for (int off = 16; off; off >>= 1) {
+        Ea += __shfl_xor_sync(0xFFFFFFFFu, Ea, off);
+        Eb += __shfl_xor_sync(0xFFFFFFFFu, Eb, off);
+    }
+    if ((tid & 31) == 0) {
+        sh_E[0][tid >> 5] = Ea;
+        sh_E[1][tid >> 5] = Eb;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        long long ta = 0, tb = 0;
+        for (int w = 0; w < NT / 32; ++w) {
+            ta += sh_E[0][w];
+            tb += sh_E[1][w];
+        }
+        a.E[sa] = (int32_t)(ta / 2);
+        a.E[sb] = (int32_t)(tb / 2);
+        atomicAdd(&a.pairs[a.k], 1);
+        atomicAdd(&a.flips[a.k], (unsigned long long)csize);
+    }
+}
+
+// -------------------------------------------------------------- adaptive ---
+__global__ void k_ad_partials(AdaptArgs a) {
+    const int n_prev = a.state[0];
+    if (n_prev >= a.nmax) return;
+    __shared__ double sw[2][RS_THREADS / 32];
+    const int emin = a.emin[a.k];
+    const int base = blockIdx.x * RS_CHUNK + threadIdx.x * 4;
+    uint32_t d[4];
+    bool valid[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        valid[q] = base + q < a.R;
+        d[q] = valid[q] ? (uint32_t)(a.E[base + q] - emin) : 0u;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int j = 0; j <= a.J; ++j) {
+        int dn = 1 << (a.J - j);
+        if (dn > a.nmax - n_prev) dn = a.nmax - n_prev;
+        const double *qs = a.qpow + (size_t)(dn - 1) * 32;
+        double w[4], w2[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            double acc = 0.0;
+            if (valid[q]) {
+                acc = 1.0;
+                uint32_t dd = d[q];
+                while (dd) {
+                    const int b = __ffs(dd) - 1;
+                    acc = __dmul_rn(acc, __ldg(&qs[b]));
+                    dd &= dd - 1u;
+                }
+            }
+            w[q] = acc;
+            w2[q] = __dmul_rn(acc, acc);
+        }
+        double s = __dadd_rn(__dadd_rn(w[0], w[1]), __dadd_rn(w[2], w[3]));
+        double s2 = __dadd_rn(__dadd_rn(w2[0], w2[1]), __dadd_rn(w2[2], w2[3]));
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            s = __dadd_rn(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+            s2 = __dadd_rn(s2, __shfl_xor_sync(0xFFFFFFFFu, s2, off));
+        }
+        if (lane == 0) {
+            sw[0][warp] = s;
+            sw[1][warp] = s2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double A = sw[0][0], B = sw[1][0];
+            for (int w3 = 1; w3 < RS_THREADS / 32; ++w3) {
+                A = __dadd_rn(A, sw[0][w3]);
+                B = __dadd_rn(B, sw[1][w3]);
+            }
+            a.part[((size_t)j * 2 + 0) * a.nch + blockIdx.x] = A;
+            a.part[((size_t)j * 2 + 1) * a.nch + blockIdx.x] = B;
+        }
+        __syncthreads();
+    }
+}
+
+// Pairwise tree sum of v[0..n) padded with zeros to a power of two, computed
+// left to right with a stack of completed subtrees (same additions as the
+// level-by-level tree).
+__device__ double tree_sum_seq(const double *v, int n) {
+    double st[20];
+    int lv[20];
+    int top = 0;
+    int L = 1;
+    while (L < n) L <<= 1;
+    for (int i = 0; i < L; ++i) {
+        double x = i < n ? v[i] : 0.0;
+        int l = 0;
+        while (top > 0 && lv[top - 1] == l) {
+            x = __dadd_rn(st[top - 1], x);
+            --top;
+            ++l;
+        }
+        st[top] = x;
+        lv[top] = l;
+        ++top;
+    }
+    return st[0];
+}
+
+__global__ void k_ad_choose(AdaptArgs a) {
+    const int n_prev = a.state[0];
+    const int lane = threadIdx.x;
+    if (n_prev >= a.nmax) {
+        if (lane == 0) a.active[a.k] = 0;
+        return;
+    }
+    bool ok = false;
+    if (lane <= a.J) {
+        const double A = tree_sum_seq(a.part + ((size_t)lane * 2 + 0) * a.nch, a.nch);
+        const double B = tree_sum_seq(a.part + ((size_t)lane * 2 + 1) * a.nch, a.nch);
+        const double ess = __ddiv_rn(__dmul_rn(A, A), B);
+        ok = ess >= a.rhoR;
+    }
+    const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
+    if (lane == 0) {
+        const int j = bal ? __ffs(bal) - 1 : a.J;
+        int dn = 1 << (a.J - j);
+        if (dn > a.nmax - n_prev) dn = a.nmax - n_prev;
+        const int nk = n_prev + dn;
+        a.state[0] = nk;
+        a.qsel[a.k] = dn - 1;
+        a.tidx[a.k] = nk;
+        a.jsel[a.k] = j;
+        a.beta[a.k] = __dmul_rn((double)nk, a.delta);
+        a.active[a.k] = 1;
+    }
+}
+
+}  // namespace
+
+size_t nlm_scratch_bytes(int32_t R) { return (size_t)R * 8 + 256; }
+
+size_t nlm_smem_bytes(int32_t np) {
+    return (size_t)2 * np + 4 * (size_t)((np + 31) / 32) + 4 * (size_t)np + 16;
+}
+
+cudaError_t launch_nonlocal(const NlmArgs &a, void *scratch, cudaStream_t st, int *launches) {
+    uint32_t *keys = reinterpret_cast<uint32_t *>(scratch);
+    int32_t *order = reinterpret_cast<int32_t *>(keys + a.R);
+    const int nb = (a.R + 255) / 256;
+    k_nlm_keys<<<nb, 256, 0, st>>>(a, keys);
+    k_nlm_rank<<<nb, 256, 0, st>>>(a, keys, order);
+    *launches = 2;
+    if (a.R >= 2) {
+        const size_t smem = nlm_smem_bytes(a.g.np);
+        cudaError_t e = cudaFuncSetAttribute(k_nlm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_nlm_pair<<<a.R / 2, 256, smem, st>>>(a, order);
+        *launches = 3;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adapt(const AdaptArgs &a, cudaStream_t st) {
+    k_ad_partials<<<a.nch, RS_THREADS, 0, st>>>(a);
+    k_ad_choose<<<1, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace pa

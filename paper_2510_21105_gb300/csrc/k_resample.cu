@@ -1,0 +1,246 @@
+// k_resample.cu -- population initialisation, local fields / energies, and the
+// per-temperature-step reweighting + resampling of PAMC (Sec. 3 of arXiv
+// 2510.21105 names population annealing; the scheme below is the library's
+// reading of it).
+//
+// Resampling of step k (energies E_r of the R replicas entering the step):
+//   E_min = min_r E_r, d_r = E_r - E_min
+//   w_r   = q^{d_r}, q = exp(-(beta_k - beta_{k-1})), as the product of the
+//           host-computed squarings q^(2^b) over the set bits b of d_r in
+//           ascending b (FP64, round to nearest, no fused operations)
+//   A     = sum of w_r as a pairwise tree over slots padded to a power of two
+//   t_r   = floor(2^32 w_r) (integer weights), T = sum t_r, P_r = sum_{s<r} t_s
+//   new slots [F(P_r), F(P_r + t_r)) copy replica r, with the systematic
+//   count F(P) = floor((P R 2^32 + o T) / (T 2^32)) and o the Philox word of
+//   (0, 0, k, tag 1). Sum of copies is exactly R.
+// Three kernels per step over chunks of RS_CHUNK slots: minimum, weights
+// (chunk tree sums of w, chunk totals and local prefixes of t), parents.
+#include "pa_internal.cuh"
+
+namespace pa {
+namespace {
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void k_init_spins(GraphDev g, int8_t *spins, int32_t Rpad, uint32_t k0, uint32_t k1) {
+    const int nchunk = g.np >> 2;
+    const long total = (long)(Rpad >> 2) * nchunk;
+    for (long idx = (long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (long)gridDim.x * blockDim.x) {
+        const int grp = (int)(idx / nchunk), c = (int)(idx % nchunk);
+        uint32_t out[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int p = 4 * c + j;
+            if (p < g.n) {
+                const uint4 u = philox10(make_uint4(g.vid[p], (uint32_t)grp, 0u, TAG_INIT), k0, k1);
+                const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) out[q] |= ((uu[q] >> 31) ? 0x01u : 0xFFu) << (8 * j);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            *reinterpret_cast<uint32_t *>(spins + (size_t)(4 * grp + q) * g.np + 4 * c) = out[q];
+    }
+}
+
+// One CTA per replica: h_p = sum_j w_pj x_j and E = 1/2 sum_p x_p h_p.
+__global__ void k_fields_energy(GraphDev g, const int8_t *spins, int16_t *fields, int32_t *E) {
+    const int r = blockIdx.x;
+    const int8_t *x = spins + (size_t)r * g.np;
+    int16_t *h = fields + (size_t)r * g.np;
+    long long acc = 0;
+    for (int p = threadIdx.x; p < g.np; p += blockDim.x) {
+        int hp = 0;
+        if (p < g.n) {
+            const uint32_t e1 = g.rp[p + 1];
+            for (uint32_t e = g.rp[p]; e < e1; ++e) {
+                const int xj = x[g.col[e]];
+                hp += g.wt ? (int)g.wt[e] * xj : xj;
+            }
+            acc += (long long)x[p] * hp;
+        }
+        h[p] = (int16_t)hp;
+    }
+    __shared__ long long red[32];
+    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        E[r] = (int32_t)(t / 2);
+    }
+}
+
+__global__ void k_rs_min(ResampleArgs a) {
+    if (a.active && !a.active[a.k]) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.stamp[a.k] = gtimer();
+    const int base = blockIdx.x * RS_CHUNK + threadIdx.x * 4;
+    int v = 0x7FFFFFFF;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (base + q < a.R) v = min(v, a.E[base + q]);
+    v = __reduce_min_sync(0xFFFFFFFFu, v);
+    if ((threadIdx.x & 31) == 0) atomicMin(&a.emin[a.k], v);
+}
+
+__global__ void k_rs_weights(ResampleArgs a) {
+    if (a.active && !a.active[a.k]) return;
+    __shared__ double qs[32];
+    __shared__ double wsum[RS_THREADS / 32];
+    __shared__ unsigned long long tsum[RS_THREADS / 32];
+    const int row = a.qsel ? a.qsel[a.k] : a.k;
+    if (threadIdx.x < 32) qs[threadIdx.x] = a.qpow[(size_t)row * 32 + threadIdx.x];
+    __syncthreads();
+    const int emin = a.emin[a.k];
+    const int base = blockIdx.x * RS_CHUNK + threadIdx.x * 4;
+    double w[4];
+    unsigned long long t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        w[q] = 0.0;
+        t[q] = 0ull;
+        if (base + q < a.R) {
+            uint32_t d = (uint32_t)(a.E[base + q] - emin);
+            double acc = 1.0;
+            while (d) {
+                const int b = __ffs(d) - 1;
+                acc = __dmul_rn(acc, qs[b]);
+                d &= d - 1u;
+            }
+            w[q] = acc;
+            t[q] = (unsigned long long)__dmul_rn(acc, 4294967296.0);
+        }
+    }
+    // Pairwise tree: (w0 + w1) + (w2 + w3), then lane butterflies, then warps.
+    double s = __dadd_rn(__dadd_rn(w[0], w[1]), __dadd_rn(w[2], w[3]));
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) s = __dadd_rn(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+    // Exclusive prefix of t over the chunk.
+    unsigned long long tt = t[0] + t[1] + t[2] + t[3];
+    unsigned long long inc = tt;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) {
+        wsum[warp] = s;
+        tsum[warp] = inc;
+    }
+    __syncthreads();
+    unsigned long long pre = inc - tt;
+    for (int w2 = 0; w2 < warp; ++w2) pre += tsum[w2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        a.ploc[base + q] = pre;     // sized nch * RS_CHUNK; slots past R hold t = 0
+        a.tval[base + q] = t[q];
+        pre += t[q];
+    }
+    if (threadIdx.x == 0) {
+        double c = wsum[0];
+        for (int w2 = 1; w2 < RS_THREADS / 32; ++w2) c = __dadd_rn(c, wsum[w2]);   // two warps: one level
+        unsigned long long ct = 0;
+        for (int w2 = 0; w2 < RS_THREADS / 32; ++w2) ct += tsum[w2];
+        a.partA[blockIdx.x] = c;
+        a.partT[blockIdx.x] = ct;
+    }
+}
+
+// floor((P R 2^32 + o T) / (T 2^32)) for R <= 65536; written as
+// floor(P R / T) + [ (P R mod T) 2^32 >= T (2^32 - o) ].
+__device__ __forceinline__ int32_t systematic_count(unsigned long long P, int32_t R,
+                                                    unsigned long long T, uint32_t o) {
+    if (P >= T) return R;
+    const unsigned long long X = P * (unsigned long long)R;
+    const unsigned long long q = X / T, r = X - q * T;
+    const unsigned __int128 lhs = (unsigned __int128)r << 32;
+    const unsigned __int128 rhs = (unsigned __int128)T * (0x100000000ull - (unsigned long long)o);
+    return (int32_t)(q + (lhs >= rhs ? 1ull : 0ull));
+}
+
+__global__ void k_rs_parents(ResampleArgs a) {
+    if (a.active && !a.active[a.k]) return;
+    __shared__ double tree[256];
+    __shared__ unsigned long long sh_T, sh_off;
+    __shared__ uint32_t sh_o;
+    if (threadIdx.x == 0) {
+        int L = 1;
+        while (L < a.nch) L <<= 1;
+        for (int c = 0; c < L; ++c) tree[c] = c < a.nch ? a.partA[c] : 0.0;
+        for (; L > 1; L >>= 1)
+            for (int i = 0; i < L / 2; ++i) tree[i] = __dadd_rn(tree[2 * i], tree[2 * i + 1]);
+        unsigned long long T = 0, off = 0;
+        for (int c = 0; c < a.nch; ++c) {
+            if (c == (int)blockIdx.x) off = T;
+            T += a.partT[c];
+        }
+        sh_T = T;
+        sh_off = off;
+        sh_o = philox10(make_uint4(0u, 0u, (uint32_t)a.k, TAG_RESAMPLE), a.key0, a.key1).x;
+        if (blockIdx.x == 0) {
+            a.recA[a.k] = tree[0];
+            a.recT[a.k] = T;
+            a.reco[a.k] = sh_o;
+        }
+    }
+    __syncthreads();
+    const unsigned long long T = sh_T, off = sh_off;
+    const uint32_t o = sh_o;
+    const int base = blockIdx.x * RS_CHUNK + threadIdx.x * 4;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = base + q;
+        if (r < a.R) {
+            const unsigned long long P = off + a.ploc[r];
+            const int32_t lo = systematic_count(P, a.R, T, o);
+            const int32_t hi = systematic_count(P + a.tval[r], a.R, T, o);
+            for (int s = lo; s < hi; ++s) a.parent[s] = r;
+            if (a.counts) a.counts[(size_t)a.k * a.R + r] = hi - lo;
+        }
+    }
+}
+
+__global__ void k_stamp(unsigned long long *stamp) { *stamp = gtimer(); }
+
+}  // namespace
+
+cudaError_t launch_init(const GraphDev &g, int8_t *spins, int32_t Rpad, uint32_t key0,
+                        uint32_t key1, cudaStream_t st) {
+    const long total = (long)(Rpad >> 2) * (g.np >> 2);
+    long blocks = (total + 255) / 256;
+    if (blocks > 65535L * 16) blocks = 65535L * 16;
+    k_init_spins<<<(unsigned)blocks, 256, 0, st>>>(g, spins, Rpad, key0, key1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields(const GraphDev &g, const int8_t *spins, int16_t *fields, int32_t *E,
+                          int32_t Rpad, cudaStream_t st) {
+    k_fields_energy<<<Rpad, 256, 0, st>>>(g, spins, fields, E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rs_min(const ResampleArgs &a, cudaStream_t st) {
+    k_rs_min<<<a.nch, RS_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rs_rest(const ResampleArgs &a, cudaStream_t st) {
+    k_rs_weights<<<a.nch, RS_THREADS, 0, st>>>(a);
+    k_rs_parents<<<a.nch, RS_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stamp(unsigned long long *stamp, cudaStream_t st) {
+    k_stamp<<<1, 1, 0, st>>>(stamp);
+    return cudaGetLastError();
+}
+
+}  // namespace pa

@@ -1,0 +1,327 @@
+// k_sweep.cu -- colour-ordered Metropolis sweeps of PAMC (Sec. 3 of arXiv
+// 2510.21105; the paper names the method but not the sweep, so the rule is
+// the library's reading: standard Metropolis on the Ising form of Eq. 1).
+//
+// One CTA holds a block of B = 4G replicas in shared memory while it runs all
+// S sweeps of one temperature step on them:
+//   S_sm[p][g]  uint32: int8 spins of replicas 4g..4g+3 at position p
+//   H_sm[p][g]  local fields of the same replicas, biased to unsigned:
+//               16-bit: two uint32 words (replicas 0,1 | 2,3), h + 32768
+//                8-bit: one uint32 word, h + 128 (max degree <= 127)
+// A colour class is an independent set, so all of its positions update in
+// parallel (one thread per (position, group)); the accepted flips push
+// +-2 into the neighbours' fields with one packed 32-bit shared atomic per
+// neighbour and group (the bias keeps every lane non-negative, so the packed
+// add never carries across lanes). One Philox4x32-10 call yields the four
+// uniforms of the group: word q of Philox(counter = (vertex, slot/4, step,
+// sweep)) belongs to slot 4*(slot/4) + q.
+// The block is loaded from the parents chosen by the resampling (the copy of
+// the resampling is fused into this load) and written to the next buffers.
+#include "pa_internal.cuh"
+
+namespace pa {
+namespace {
+
+__device__ __forceinline__ void transpose4x4_bytes(uint32_t w0, uint32_t w1, uint32_t w2,
+                                                   uint32_t w3, uint32_t o[4]) {
+    const uint32_t a_lo = __byte_perm(w0, w1, 0x5140);
+    const uint32_t a_hi = __byte_perm(w0, w1, 0x7362);
+    const uint32_t b_lo = __byte_perm(w2, w3, 0x5140);
+    const uint32_t b_hi = __byte_perm(w2, w3, 0x7362);
+    o[0] = __byte_perm(a_lo, b_lo, 0x5410);
+    o[1] = __byte_perm(a_lo, b_lo, 0x7632);
+    o[2] = __byte_perm(a_hi, b_hi, 0x5410);
+    o[3] = __byte_perm(a_hi, b_hi, 0x7632);
+}
+
+template <int G, int FB, bool WEIGHTED>
+__device__ __forceinline__ void sweep_item(uint32_t *__restrict__ Ssm, uint32_t *__restrict__ Hsm,
+                                           const uint32_t *__restrict__ Tt, const SweepArgs &a,
+                                           int p, int g, uint32_t c1, uint32_t c3, uint32_t vmask,
+                                           int dE[4], uint32_t &nacc) {
+    const int widx = p * G + g;
+    const uint32_t sw = Ssm[widx];
+    uint32_t hw0, hw1 = 0;
+    if (FB == 16) {
+        const uint2 hv = reinterpret_cast<const uint2 *>(Hsm)[widx];
+        hw0 = hv.x;
+        hw1 = hv.y;
+    } else {
+        hw0 = Hsm[widx];
+    }
+    int m[4], x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        x[q] = (int)(int8_t)(sw >> (8 * q));
+        int h;
+        if (FB == 16)
+            h = (int)(((q < 2 ? hw0 : hw1) >> (16 * (q & 1))) & 0xFFFFu) - 32768;
+        else
+            h = (int)((hw0 >> (8 * q)) & 0xFFu) - 128;
+        m[q] = x[q] > 0 ? -h : h;   // dE = -2 x h = 2m
+    }
+    const uint4 u = philox10(make_uint4(__ldg(&a.g.vid[p]), c1, (uint32_t)a.k, c3), a.key0, a.key1);
+    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+    uint32_t acc = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool ok = (m[q] <= 0) || (uu[q] < Tt[min(m[q], a.g.mmax)]);
+        acc |= (uint32_t)ok << q;
+    }
+    if (acc) {
+        uint32_t flip = 0;
+        int d[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool f = (acc >> q) & 1u;
+            flip |= f ? (0xFEu << (8 * q)) : 0u;
+            dE[q] += f ? 2 * m[q] : 0;
+            d[q] = f ? -2 * x[q] : 0;
+        }
+        Ssm[widx] = sw ^ flip;
+        nacc += __popc(acc & vmask);
+        uint32_t D0, D1 = 0;
+        if (FB == 16) {
+            D0 = (uint32_t)(d[0] + d[1] * 65536);
+            D1 = (uint32_t)(d[2] + d[3] * 65536);
+        } else {
+            D0 = (uint32_t)(d[0] + d[1] * 256 + d[2] * 65536 + d[3] * 16777216);
+        }
+        const uint32_t e0 = __ldg(&a.g.rp[p]), e1 = __ldg(&a.g.rp[p + 1]);
+        for (uint32_t e = e0; e < e1; ++e) {
+            const int j = __ldg(&a.g.col[e]);
+            uint32_t s0 = D0, s1 = D1;
+            if (WEIGHTED) {
+                if (__ldg(&a.g.wt[e]) < 0) {
+                    s0 = 0u - D0;
+                    s1 = 0u - D1;
+                }
+            }
+            if (FB == 16) {
+                atomicAdd(&Hsm[2 * (j * G + g)], s0);
+                atomicAdd(&Hsm[2 * (j * G + g) + 1], s1);
+            } else {
+                atomicAdd(&Hsm[j * G + g], s0);
+            }
+        }
+    }
+}
+
+template <int G, int FB, bool WEIGHTED>
+__global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    // A step after the adaptive schedule has ended only carries the population over.
+    const bool act = !a.active || a.active[a.k];
+    const int nsweeps = act ? a.S : 0;
+    const int np = a.g.np;
+    constexpr int HW = (FB == 16) ? 2 : 1;
+    uint32_t *Ssm = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *Hsm = Ssm + (size_t)np * G;
+    uint32_t *Tt = Hsm + (size_t)np * G * HW;
+    const int tsz = (a.g.mmax + 1 + 3) & ~3;
+    int32_t *cls = reinterpret_cast<int32_t *>(Tt + tsz);
+    const int csz = (a.g.ncol + 1 + 3) & ~3;
+    int32_t *Eacc = cls + csz;          // [4G]
+    int32_t *PS = Eacc + 4 * G;         // [4G] parent slot of each replica
+    int32_t *misc = PS + 4 * G;         // best E, step, sweep, slot, copy-from (q+1), changed
+
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
+    const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
+    for (int i = tid; i <= a.g.mmax; i += NT) Tt[i] = tab[i];
+    for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
+    const int gthr = tid % G;   // NT is a multiple of 32, so each thread keeps one group
+
+    for (int blk = blockIdx.x; blk < a.nblk; blk += gridDim.x) {
+        const int slot0 = blk * 4 * G;
+        if (tid < 4 * G) PS[tid] = act ? a.parent[slot0 + tid] : slot0 + tid;
+        if (tid == 0) {
+            const int4 br = a.best_rec[blk];
+            misc[0] = br.x; misc[1] = br.y; misc[2] = br.z; misc[3] = br.w;
+            misc[4] = 0; misc[5] = 0;
+        }
+        __syncthreads();
+        if (tid < 4 * G) Eacc[tid] = a.E_in[PS[tid]];
+        // Load the block, transposing replica rows into position-major words.
+        for (int idx = tid; idx < (np >> 2) * G; idx += NT) {
+            const int g = idx % G, c = idx / G;
+            uint32_t w[4];
+            uint2 f[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const size_t row = (size_t)PS[4 * g + q] * np + 4 * c;
+                w[q] = __ldg(reinterpret_cast<const uint32_t *>(a.spins_in + row));
+                f[q] = __ldg(reinterpret_cast<const uint2 *>(a.fields_in + row));
+            }
+            uint32_t o[4];
+            transpose4x4_bytes(w[0], w[1], w[2], w[3], o);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Ssm[(4 * c + j) * G + g] = o[j];
+            if (FB == 16) {
+                uint2 *H2 = reinterpret_cast<uint2 *>(Hsm);
+                H2[(4 * c + 0) * G + g] = make_uint2(__byte_perm(f[0].x, f[1].x, 0x5410) ^ 0x80008000u,
+                                                     __byte_perm(f[2].x, f[3].x, 0x5410) ^ 0x80008000u);
+                H2[(4 * c + 1) * G + g] = make_uint2(__byte_perm(f[0].x, f[1].x, 0x7632) ^ 0x80008000u,
+                                                     __byte_perm(f[2].x, f[3].x, 0x7632) ^ 0x80008000u);
+                H2[(4 * c + 2) * G + g] = make_uint2(__byte_perm(f[0].y, f[1].y, 0x5410) ^ 0x80008000u,
+                                                     __byte_perm(f[2].y, f[3].y, 0x5410) ^ 0x80008000u);
+                H2[(4 * c + 3) * G + g] = make_uint2(__byte_perm(f[0].y, f[1].y, 0x7632) ^ 0x80008000u,
+                                                     __byte_perm(f[2].y, f[3].y, 0x7632) ^ 0x80008000u);
+            } else {
+                const uint32_t px01 = __byte_perm(f[0].x, f[1].x, 0x6420);
+                const uint32_t px23 = __byte_perm(f[2].x, f[3].x, 0x6420);
+                const uint32_t py01 = __byte_perm(f[0].y, f[1].y, 0x6420);
+                const uint32_t py23 = __byte_perm(f[2].y, f[3].y, 0x6420);
+                Hsm[(4 * c + 0) * G + g] = __byte_perm(px01, px23, 0x6420) ^ 0x80808080u;
+                Hsm[(4 * c + 1) * G + g] = __byte_perm(px01, px23, 0x7531) ^ 0x80808080u;
+                Hsm[(4 * c + 2) * G + g] = __byte_perm(py01, py23, 0x6420) ^ 0x80808080u;
+                Hsm[(4 * c + 3) * G + g] = __byte_perm(py01, py23, 0x7531) ^ 0x80808080u;
+            }
+        }
+        __syncthreads();
+
+        uint32_t vmask = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vmask |= (slot0 + 4 * gthr + q < a.R) ? (1u << q) : 0u;
+        const uint32_t c1 = (uint32_t)(blk * G + gthr);
+        uint32_t nacc = 0;
+        for (int s = 0; s < nsweeps; ++s) {
+            const uint32_t c3 = TAG_SWEEP | (uint32_t)s;
+            int dE[4] = {0, 0, 0, 0};
+            for (int c = 0; c < a.g.ncol; ++c) {
+                const int p0 = cls[c];
+                const int cnt = (cls[c + 1] - p0) * G;
+                for (int idx = tid; idx < cnt; idx += NT)
+                    sweep_item<G, FB, WEIGHTED>(Ssm, Hsm, Tt, a, p0 + idx / G, gthr, c1, c3, vmask,
+                                                dE, nacc);
+                __syncthreads();
+            }
+            // Energies after sweep s: reduce the per-thread changes of each replica.
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                int v = dE[q];
+#pragma unroll
+                for (int off = G; off < 32; off <<= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+                if (lane < G && v != 0) atomicAdd(&Eacc[4 * lane + q], v);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int bq = -1, bE = 0x7FFFFFFF;
+                for (int q = 0; q < 4 * G; ++q)
+                    if (slot0 + q < a.R && Eacc[q] < bE) { bE = Eacc[q]; bq = q; }
+                misc[4] = 0;
+                if (bq >= 0) {
+                    atomicMin(&a.sweep_emin[(size_t)a.k * a.S + s], bE);
+                    if (bE < misc[0]) {
+                        misc[0] = bE; misc[1] = a.k; misc[2] = s; misc[3] = slot0 + bq;
+                        misc[4] = bq + 1; misc[5] = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            if (misc[4]) {   // block-uniform: copy the new best configuration
+                const int q = misc[4] - 1, g = q >> 2, sh = 8 * (q & 3);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(a.best_cfg + (size_t)blk * np);
+                for (int c = tid; c < (np >> 2); c += NT) {
+                    uint32_t v = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) v |= ((Ssm[(4 * c + j) * G + g] >> sh) & 0xFFu) << (8 * j);
+                    dst[c] = v;
+                }
+                __syncthreads();
+            }
+        }
+        // Store the block to the next population buffers.
+        for (int idx = tid; idx < (np >> 2) * G; idx += NT) {
+            const int g = idx % G, c = idx / G;
+            uint32_t o[4];
+            transpose4x4_bytes(Ssm[(4 * c + 0) * G + g], Ssm[(4 * c + 1) * G + g],
+                               Ssm[(4 * c + 2) * G + g], Ssm[(4 * c + 3) * G + g], o);
+            uint2 f[4];
+            if (FB == 16) {
+                const uint2 *H2 = reinterpret_cast<const uint2 *>(Hsm);
+                const uint2 h0 = H2[(4 * c + 0) * G + g], h1 = H2[(4 * c + 1) * G + g];
+                const uint2 h2 = H2[(4 * c + 2) * G + g], h3 = H2[(4 * c + 3) * G + g];
+                const uint32_t L0 = h0.x ^ 0x80008000u, L1 = h1.x ^ 0x80008000u;
+                const uint32_t L2 = h2.x ^ 0x80008000u, L3 = h3.x ^ 0x80008000u;
+                const uint32_t U0 = h0.y ^ 0x80008000u, U1 = h1.y ^ 0x80008000u;
+                const uint32_t U2 = h2.y ^ 0x80008000u, U3 = h3.y ^ 0x80008000u;
+                f[0] = make_uint2(__byte_perm(L0, L1, 0x5410), __byte_perm(L2, L3, 0x5410));
+                f[1] = make_uint2(__byte_perm(L0, L1, 0x7632), __byte_perm(L2, L3, 0x7632));
+                f[2] = make_uint2(__byte_perm(U0, U1, 0x5410), __byte_perm(U2, U3, 0x5410));
+                f[3] = make_uint2(__byte_perm(U0, U1, 0x7632), __byte_perm(U2, U3, 0x7632));
+            } else {
+                uint32_t P[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) P[j] = Hsm[(4 * c + j) * G + g] ^ 0x80808080u;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    int h[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) h[j] = (int)(int8_t)(P[j] >> (8 * q));
+                    f[q] = make_uint2(((uint32_t)h[0] & 0xFFFFu) | ((uint32_t)h[1] << 16),
+                                      ((uint32_t)h[2] & 0xFFFFu) | ((uint32_t)h[3] << 16));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const size_t row = (size_t)(slot0 + 4 * g + q) * np + 4 * c;
+                *reinterpret_cast<uint32_t *>(a.spins_out + row) = o[q];
+                *reinterpret_cast<uint2 *>(a.fields_out + row) = f[q];
+            }
+        }
+        if (tid < 4 * G) a.E_out[slot0 + tid] = Eacc[tid];
+        if (tid == 0 && misc[5]) a.best_rec[blk] = make_int4(misc[0], misc[1], misc[2], misc[3]);
+        const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, nacc);
+        if (act && lane == 0 && wsum) atomicAdd(&a.accepts[a.k], (unsigned long long)wsum);
+        __syncthreads();
+    }
+}
+
+template <int G, int FB, bool W>
+void *kernel_ptr() {
+    return reinterpret_cast<void *>(&k_sweep<G, FB, W>);
+}
+
+void *select_kernel(int G, int fb, bool weighted) {
+    if (G == 1) {
+        if (fb == 16) return weighted ? kernel_ptr<1, 16, true>() : kernel_ptr<1, 16, false>();
+        return weighted ? kernel_ptr<1, 8, true>() : kernel_ptr<1, 8, false>();
+    }
+    if (fb == 16) return weighted ? kernel_ptr<2, 16, true>() : kernel_ptr<2, 16, false>();
+    return weighted ? kernel_ptr<2, 8, true>() : kernel_ptr<2, 8, false>();
+}
+
+}  // namespace
+
+cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int threads,
+                            bool weighted, SweepConfig *cfg) {
+    const int HW = field_bits == 16 ? 2 : 1;
+    size_t smem = (size_t)g.np * G * 4 * (1 + HW);
+    smem += (size_t)((g.mmax + 1 + 3) & ~3) * 4;
+    smem += (size_t)((g.ncol + 1 + 3) & ~3) * 4;
+    smem += (size_t)(8 * G + 8) * 4;
+    void *fn = select_kernel(G, field_bits, weighted);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    const int nblk = (R + 4 * G - 1) / (4 * G);
+    cfg->G = G;
+    cfg->field_bits = field_bits;
+    cfg->threads = threads;
+    cfg->smem = smem;
+    cfg->grid = nblk < occ * sms ? nblk : occ * sms;
+    return cudaSuccess;
+}
+
+cudaError_t launch_sweep(const SweepConfig &cfg, const SweepArgs &a, cudaStream_t st) {
+    void *fn = select_kernel(cfg.G, cfg.field_bits, a.g.wt != nullptr);
+    void *args[] = {const_cast<SweepArgs *>(&a)};
+    return cudaLaunchKernel(fn, dim3(cfg.grid), dim3(cfg.threads), args, cfg.smem, st);
+}
+
+}  // namespace pa

@@ -1,0 +1,120 @@
+// pa_internal.cuh -- internal declarations of libpa.so (not part of the ABI).
+//
+// Device layout of one anneal (vertices renumbered by colour; "position" p
+// is a vertex's index in that order, np = n rounded up to 16):
+//   spins  int8  [Rpad][np]   +1/-1, ping-pong pair (cur / next)
+//   fields int16 [Rpad][np]   h_p = sum_j w_pj x_j, ping-pong pair
+//   E      int32 [Rpad]       Ising energy of each replica, ping-pong pair
+//   parent int32 [Rpad]       new slot -> old slot of the current step
+// Rpad rounds R up to the replica block of the sweep kernel; padding slots
+// copy themselves and are excluded from every reduction.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pa {
+
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
+// multiplies by 0xD2511F53 / 0xCD9E8D57, high halves xored with the other
+// counter words and the key; key advanced by 0x9E3779B9 / 0xBB67AE85.
+__host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+#ifdef __CUDA_ARCH__
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+#else
+        const uint32_t hi0 = (uint32_t)(((uint64_t)0xD2511F53u * c.x) >> 32);
+        const uint32_t hi1 = (uint32_t)(((uint64_t)0xCD9E8D57u * c.z) >> 32);
+#endif
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Stream tags in the top four bits of counter word 3.
+constexpr uint32_t TAG_SWEEP = 0u << 28;
+constexpr uint32_t TAG_RESAMPLE = 1u << 28;
+constexpr uint32_t TAG_NONLOCAL = 2u << 28;
+constexpr uint32_t TAG_INIT = 3u << 28;
+
+constexpr int32_t EMIN_SENTINEL = 0x7F7F7F7F;  // byte-fillable "+infinity"
+constexpr int RS_CHUNK = 256;                   // slots per resampling CTA (power of two)
+constexpr int RS_THREADS = 64;                  // 4 slots per thread
+
+struct GraphDev {
+    int32_t n, np, ncol, mmax;
+    const uint32_t *rp;   // [n+1] row pointers, position order
+    const uint16_t *col;  // [2M] neighbour positions
+    const int8_t *wt;     // [2M] weights or nullptr (all +1)
+    const uint32_t *vid;  // [n] original vertex of each position
+    const int32_t *cls;   // [ncol+1] colour class boundaries in positions
+};
+
+struct SweepArgs {
+    GraphDev g;
+    const int8_t *spins_in;
+    const int16_t *fields_in;
+    const int32_t *E_in;
+    int8_t *spins_out;
+    int16_t *fields_out;
+    int32_t *E_out;
+    const int32_t *parent;       // [Rpad]
+    const uint32_t *tables;      // [ntables][mmax+1] acceptance thresholds
+    const int32_t *tidx;         // [K] table used by step k
+    const int32_t *active;       // [K] 0 = skip the step (adaptive end), may be null
+    int32_t R, nblk, S, k;
+    uint32_t key0, key1;
+    int4 *best_rec;              // [nblk] (E, step, sweep, slot) per replica block
+    int8_t *best_cfg;            // [nblk][np] configuration of that record
+    unsigned long long *accepts; // [K] accepted flips per step
+    int32_t *sweep_emin;         // [K][S] minimum energy per sweep end
+};
+
+struct ResampleArgs {
+    const int32_t *E;            // [Rpad] energies entering the step
+    int32_t R, nch, k;
+    uint32_t key0, key1;
+    const double *qpow;          // [K][32] squarings of q_k, or per-dn table (adaptive)
+    const int32_t *qsel;         // adaptive: row of qpow for step k (nullptr: row k)
+    const int32_t *active;       // [K] or nullptr
+    int32_t *emin;               // [K]
+    double *partA;               // [nch]
+    unsigned long long *partT;   // [nch]
+    unsigned long long *tval;    // [Rpad]
+    unsigned long long *ploc;    // [Rpad]
+    int32_t *parent;             // [Rpad]
+    double *recA;                // [K]
+    unsigned long long *recT;    // [K]
+    uint32_t *reco;              // [K]
+    int32_t *counts;             // [K][R] or nullptr
+    unsigned long long *stamp;   // [K+1] globaltimer at the start of each step
+};
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_init(const GraphDev &g, int8_t *spins, int32_t Rpad, uint32_t key0,
+                        uint32_t key1, cudaStream_t st);
+cudaError_t launch_fields(const GraphDev &g, const int8_t *spins, int16_t *fields, int32_t *E,
+                          int32_t Rpad, cudaStream_t st);
+// Minimum of the energies (and the step's start stamp), then weights + parents.
+cudaError_t launch_rs_min(const ResampleArgs &a, cudaStream_t st);
+cudaError_t launch_rs_rest(const ResampleArgs &a, cudaStream_t st);
+cudaError_t launch_stamp(unsigned long long *stamp, cudaStream_t st);
+
+struct SweepConfig {
+    int G;          // replica groups of 4 per CTA (1 or 2)
+    int field_bits; // 16 or 8
+    int threads;
+    int grid;
+    size_t smem;
+};
+cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int threads,
+                            bool weighted, SweepConfig *cfg);
+cudaError_t launch_sweep(const SweepConfig &cfg, const SweepArgs &a, cudaStream_t st);
+
+}  // namespace pa

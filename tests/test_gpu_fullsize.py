@@ -1,0 +1,90 @@
+"""Parity at the full benchmark sizes, in the launch configuration the
+benchmark times: the GPU runs the real workload up to step k, its population
+is dumped, and the oracle replays step k (resampling from the full energy
+vector, then the sweeps and non-local moves of sampled slots) for comparison
+with the GPU's population after step k."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import require_gpu
+from paper_2510_21105_gb300 import binding as B
+from paper_2510_21105_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def _replay_check(g, betas, R, S, seed, k, subset, nlm_period=0):
+    a = B.Annealer.from_graph(g)
+    a.begin(betas, R, S, seed, record_counts=1, nlm_period=nlm_period)
+    a.run(k)
+    a.sync()
+    spins_a, E_a = a.state()
+    a.run(k + 1)
+    a.sync()
+    spins_b, E_b = a.state()
+    counts = a.step_stats(counts=True)["counts"][k]
+    a.close()
+    nlm_now = nlm_period > 0 and k > 0 and k % nlm_period == 0
+    rep = oracle.step_replay(g.rp, g.col, g.w, spins_a, S, seed, k, betas[k - 1] if k else 0.0,
+                             betas[k], subset, nlm_now=nlm_now)
+    np.testing.assert_array_equal(counts, rep["counts"], err_msg="copy counts at full size")
+    assert counts.sum() == R
+    np.testing.assert_array_equal(spins_b[subset], rep["spins"], err_msg="replayed spins")
+    np.testing.assert_array_equal(E_b[subset], rep["E"], err_msg="replayed energies")
+    for s in subset[:4]:   # energies carried by the GPU equal a full recomputation
+        assert oracle.energy(g.rp, g.col, g.w, spins_b[s]) == E_b[s]
+    return E_a
+
+
+def test_replay_g63like_full_population():
+    c = wl.CONFIGS["g63like"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    subset = np.array([0, 1, 2, 3, 4097, 8190, 12345, 16383])
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], 3, subset)
+
+
+def test_replay_g63like_nonlocal_step():
+    c = wl.CONFIGS["g63like"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    k = c["nlm_period"]
+    order = oracle.nlm_order(c["R"], c["seed"], k)
+    subset = np.array(sorted(order[[0, 1, 2000, 2001, 16382, 16383]].tolist()))
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], k, subset, nlm_period=k)
+
+
+def test_replay_torus100_full_population():
+    c = wl.CONFIGS["torus100"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    subset = np.array([0, 5, 31, 32767, 20000])
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], 4, subset)
+
+
+def test_full_g63like_anneal_properties():
+    """The whole benchmarked anneal: invariants that hold at any size."""
+    c = wl.CONFIGS["g63like"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    a = B.Annealer.from_graph(g)
+    a.anneal(betas, c["R"], c["S"], c["seed"], nlm_period=c["nlm_period"])
+    cut, cfg, step, sweep = a.best()
+    Eb, sb, swb, slot = a.best_record()
+    st = a.stats()
+    rec = a.step_stats()
+    a.close()
+    W = oracle.total_weight(g.rp, g.col, g.w)
+    assert oracle.energy(g.rp, g.col, g.w, cfg) == Eb and cut == (W - Eb) // 2
+    assert Eb == rec["sweep_emin"].min()
+    assert st["steps_run"] == c["K"] and st["attempts"] == g.n * c["R"] * c["S"] * c["K"]
+    assert np.all(rec["nlm_pairs"][c["nlm_period"]::c["nlm_period"]] > 0)
+    assert np.all(rec["T"] > 0)
+    # a G63-shaped random graph: the cut should be far above the random-cut value M/2
+    assert cut > 0.62 * g.m

@@ -1,0 +1,151 @@
+"""GPU path vs oracle, element by element, through the C-ABI (bit-exact:
+spins, energies, copy counts, weight sums, best record and configuration)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_helpers import assert_parity, require_gpu, run_gpu, run_oracle
+from paper_2510_21105_gb300 import binding as B
+from paper_2510_21105_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    require_gpu()
+
+
+def test_tables_and_colouring_match_oracle():
+    g = wl.gnp(300, 0.07, seed=3)
+    betas = wl.linear_betas(0.1, 3.0, 9)
+    a = B.Annealer.from_graph(g)
+    a.begin(betas, R=8, S=1, seed=1)
+    for k in range(9):
+        acc, _ = a.tables(k, g.maxdeg)
+        assert np.array_equal(acc, oracle.accept_table(betas[k], g.maxdeg))
+    ncol, colour, pos = a.colouring()
+    ncol_o, colour_o = oracle.greedy_colour(g.rp, g.col)
+    assert ncol == ncol_o and np.array_equal(colour, colour_o)
+    assert sorted(pos.tolist()) == list(range(g.n))
+    a.close()
+
+
+def test_parity_gnp800_full_workload():
+    # N = 800, p = 0.06, R = 256, beta 0.1 -> 3.0 in 100 steps, 4 sweeps, seed 0.
+    c = wl.CONFIGS["gnp800"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    gpu = run_gpu(g, betas, c["R"], c["S"], c["seed"])
+    orc = run_oracle(g, betas, c["R"], c["S"], c["seed"])
+    assert_parity(gpu, orc, g, c["R"], c["S"])
+
+
+@pytest.mark.parametrize("R,opts", [(6, {}), (13, {"field_bits": 8}), (1, {}),
+                                    (24, {"replicas_per_cta": 8}),
+                                    (40, {"replicas_per_cta": 8, "field_bits": 8, "threads_per_cta": 128})])
+def test_parity_ragged_signed(R, opts):
+    g = wl.from_edges(37, *_random_edges(37, 90, seed=R), name="ragged")
+    betas = wl.linear_betas(0.05, 2.5, 7)
+    gpu = run_gpu(g, betas, R, 3, seed=1234 + R, **opts)
+    orc = run_oracle(g, betas, R, 3, seed=1234 + R)
+    assert_parity(gpu, orc, g, R, 3)
+
+
+def _random_edges(n, m, seed):
+    rng = np.random.default_rng(seed)
+    seen = set()
+    while len(seen) < m:
+        i, j = sorted(rng.integers(0, n, 2).tolist())
+        if i != j:
+            seen.add((i, j))
+    e = np.array(sorted(seen))
+    w = rng.choice(np.array([-1, 1], np.int8), size=len(e))
+    return e[:, 0], e[:, 1], w
+
+
+def test_parity_torus_two_colour_checkerboard():
+    g = wl.torus(24, seed=5)
+    betas = wl.linear_betas(0.1, 3.5, 12)
+    gpu = run_gpu(g, betas, 64, 4, seed=9)
+    orc = run_oracle(g, betas, 64, 4, seed=9)
+    assert gpu["stats"]["n_colours"] == 2
+    assert_parity(gpu, orc, g, 64, 4)
+
+
+def test_parity_nonlocal_moves():
+    g = wl.gnm(500, 3000, seed=7)
+    betas = wl.linear_betas(0.1, 3.0, 13)
+    gpu = run_gpu(g, betas, 64, 3, seed=11, nlm_period=3)
+    orc = run_oracle(g, betas, 64, 3, seed=11, nlm_period=3)
+    assert orc.step_nlm_pairs.sum() > 0
+    assert_parity(gpu, orc, g, 64, 3)
+
+
+def test_parity_adaptive_steps():
+    g = wl.gnp(120, 0.08, seed=13)
+    kw = dict(adaptive=1, rho=0.6, adapt_J=5, adapt_dbeta_max=0.25, beta_max=2.0)
+    gpu = run_gpu(g, None, 96, 2, seed=17, K=300, **kw)
+    orc = run_oracle(g, None, 96, 2, seed=17, K=300, adaptive=True, rho=0.6, adapt_J=5,
+                     adapt_dbeta_max=0.25, beta_max=2.0)
+    assert orc.steps_run < 300 and orc.step_beta[-1] == pytest.approx(2.0)
+    np.testing.assert_array_equal(gpu["rec"]["jsel"], orc.step_jsel)
+    assert_parity(gpu, orc, g, 96, 2)
+
+
+def test_degenerate_cases():
+    # Empty graph: every flip has dE = 0 and is accepted.
+    g = wl.from_edges(5, [], [])
+    betas = wl.linear_betas(0.5, 1.0, 3)
+    gpu = run_gpu(g, betas, 4, 2, seed=3)
+    orc = run_oracle(g, betas, 4, 2, seed=3)
+    assert_parity(gpu, orc, g, 4, 2)
+    # Zero sweeps: resampling only; no best exists.
+    g = wl.gnp(30, 0.2, seed=1)
+    a = B.Annealer.from_graph(g)
+    a.anneal(wl.linear_betas(0.1, 1.0, 4), R=8, S=0, seed=2)
+    with pytest.raises(B.PaError) as e:
+        a.best()
+    assert e.value.code == B.PA_ESTATE
+    a.close()
+    # Invalid schedules and sizes.
+    a = B.Annealer.from_graph(g)
+    for betas, R in [([0.5, 0.4], 8), ([0.1, np.nan], 8), ([0.1], 0), ([0.1], 70000), ([-0.1], 8)]:
+        with pytest.raises(B.PaError) as e:
+            a.anneal(np.array(betas), R=R, S=1, seed=0)
+        assert e.value.code == B.PA_EINVAL
+    a.close()
+
+
+def test_checkpoint_resume_is_bit_exact(tmp_path):
+    g = wl.gnp(200, 0.05, seed=21)
+    betas = wl.linear_betas(0.1, 2.5, 10)
+    full = B.Annealer.from_graph(g)
+    full.anneal(betas, R=32, S=3, seed=5, nlm_period=4)
+    s_full, E_full = full.state()
+    b_full = full.best_record()
+    part = B.Annealer.from_graph(g)
+    part.begin(betas, R=32, S=3, seed=5, nlm_period=4)
+    part.run(6)
+    part.sync()
+    part.save(str(tmp_path / "ck.bin"))
+    part.close()
+    res = B.Annealer.from_graph(g)
+    res.load(str(tmp_path / "ck.bin"))
+    res.run(10)
+    res.sync()
+    s_res, E_res = res.state()
+    assert np.array_equal(s_full, s_res) and np.array_equal(E_full, E_res)
+    assert res.best_record() == b_full
+    full.close()
+    res.close()
+
+
+def test_repeat_runs_are_identical_and_launch_shape_free():
+    g = wl.gnm(1000, 6000, seed=3)
+    betas = wl.linear_betas(0.2, 3.0, 6)
+    r1 = run_gpu(g, betas, 64, 3, seed=77)
+    r2 = run_gpu(g, betas, 64, 3, seed=77, threads_per_cta=256)
+    r3 = run_gpu(g, betas, 64, 3, seed=77, replicas_per_cta=8, threads_per_cta=1024)
+    for r in (r2, r3):
+        assert np.array_equal(r1["spins"], r["spins"]) and r1["best"] == r["best"]
