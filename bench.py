@@ -45,6 +45,8 @@ def parse():
     p.add_argument("--config", default="g63like")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--field-bits", type=int, default=0, help="0 = auto layout")
+    p.add_argument("--threads", type=int, default=0, help="threads per sweep CTA (0 = auto)")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="approximate CPU time of the oracle sample")
     return p.parse_args()
@@ -205,9 +207,12 @@ def run_ours(args, rank, world, dist):
 
     ann = B.Annealer.from_graph(g)
 
+    layout_bits = args.field_bits if args.field_bits else (7 if g.maxdeg <= 127 else 16)
+
     def one(time_kernels=0):
         ann.anneal(betas, R, S, seed, nlm_period=c["nlm_period"], stream=sh,
-                   time_kernels=time_kernels)
+                   time_kernels=time_kernels, field_bits=args.field_bits,
+                   threads_per_cta=args.threads)
 
     for _ in range(args.warmup):
         one()
@@ -231,6 +236,7 @@ def run_ours(args, rank, world, dist):
         dist.barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     t_best = st["t_best_ms"]
+    acc_rate = st["accepts"] / max(st["attempts"], 1)
     cut, _, best_step, _ = ann.best()
     ms_max = ms
     if dist:
@@ -257,7 +263,8 @@ def run_ours(args, rank, world, dist):
             ctx = B.C.c_void_p()
             rc = lib.pa_create(B.C.byref(ctx), g.n, rp.data_ptr(), col.data_ptr(), None)
             assert rc == 0, rc
-            o = B.pa_default_opts(nlm_period=c["nlm_period"], stream=sh)
+            o = B.pa_default_opts(nlm_period=c["nlm_period"], stream=sh, field_bits=args.field_bits,
+                                  threads_per_cta=args.threads)
             rc = lib.pa_anneal(ctx, hb.data_ptr(), K, R, S, seed, B.C.byref(o))
             assert rc == 0, rc
             cutv = B.C.c_int64()
@@ -293,6 +300,9 @@ def run_ours(args, rank, world, dist):
                                    f"beta {c['beta'][0]}->{c['beta'][1]} nlm_period={c['nlm_period']}",
                        "l2": "inputs larger than L2 (population 688 MB per buffer pair)",
                        "seed": c["seed"]},
+            "layout": {7: "packed byte (spin bit + 7-bit field)", 8: "int8 spin + int8 field",
+                       16: "int8 spin + int16 field"}.get(layout_bits, str(layout_bits)),
+            "accept_rate": acc_rate,
             "best_cut": int(cut), "best_step": int(best_step), "time_to_best_ms": t_best,
             "e2e": e2e, "gpu_launches": stats_acc["kernel_launches"],
             "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "peaks": peaks_src}

@@ -59,9 +59,13 @@ typedef struct pa_ctx pa_ctx;
 
 typedef struct {
     int32_t variant;          /* PA_VARIANT_*; default PA_VARIANT_I8 */
-    int32_t field_bits;       /* I8 variant: width of local fields in shared
-                                 memory, 16 (default) or 8 (needs max degree
-                                 <= 127) */
+    int32_t field_bits;       /* I8 variant: shared-memory layout of a replica
+                                 block: 16 = int8 spin + int16 field,
+                                 8 = int8 spin + int8 field, 7 = one packed
+                                 byte (spin bit + 7-bit field); 8 and 7 need
+                                 max degree <= 127. 0 (default) = 7 when the
+                                 degree allows, else 16. Results do not
+                                 depend on the layout. */
     int32_t nlm_period;       /* non-local (Houdayer) move after the sweeps of
                                  step k when k > 0 and k % nlm_period == 0;
                                  0 = off (default) */

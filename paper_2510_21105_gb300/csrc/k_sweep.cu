@@ -277,12 +277,285 @@ __global__ void __launch_bounds__(1024) k_sweep(const SweepArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Packed variant: one byte per (position, replica) holds the spin in bit 0 and
+// the biased local field in bits 1..7. Because h_p = sum of deg(p) terms +-1,
+// h_p + 128 has the parity of deg(p), so its low bit is redundant and is
+// replaced by the spin bit:  byte = ((h + 128) & ~1) | s,  s = (x == +1).
+// Needs max degree <= 127. Flipping a spin toggles bit 0; a neighbour flip
+// adds +-2 to the byte (bit 0 untouched), four replicas per packed atomic.
+// With m = -x h and mb = m + 128 per byte:
+//   hb = (b & 0xFE..) | par,  M = s * 0xFF,  mb = (hb ^ M) + s
+// (for s = 1 this is the bytewise negation 256 - hb; hb >= 1 so no carry).
+// A move is accepted iff mb <= 128 (m <= 0) or u < T[m].
+struct PkItem {
+    uint32_t b, mb, smask, acc;
+};
+
+__device__ __forceinline__ void pk_decide(const uint32_t *__restrict__ Bsm, const uint32_t *__restrict__ T256,
+                                          const uint32_t *__restrict__ Psm, const SweepArgs &a, int p,
+                                          uint32_t c1, uint32_t c3, PkItem &it) {
+    const uint32_t vid = __ldg(&a.g.vid[p]);
+    const uint32_t b = Bsm[p];
+    const uint32_t par = (Psm[p >> 5] >> (p & 31)) & 1u;
+    const uint32_t smask = b & 0x01010101u;
+    const uint32_t hb = (b & 0xFEFEFEFEu) | (par * 0x01010101u);
+    const uint32_t mb = (hb ^ (smask * 0xFFu)) + smask;
+    const uint4 u = philox10(make_uint4(vid, c1, (uint32_t)a.k, c3), a.key0, a.key1);
+    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+    uint32_t acc = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
+        const bool ok = (idx <= 128u) | (uu[q] < T256[idx]);
+        acc |= (uint32_t)ok << q;
+    }
+    it.b = b;
+    it.mb = mb;
+    it.smask = smask;
+    it.acc = acc;
+}
+
+// Own word, energy and acceptance bookkeeping of an item; returns the packed
+// field change D of its neighbours (0 if nothing was accepted).
+__device__ __forceinline__ uint32_t pk_commit_self(uint32_t *__restrict__ Bsm, int p, const PkItem &it,
+                                                   uint32_t vmask, int dE[4], uint32_t &nacc) {
+    if (!it.acc) return 0u;
+    const uint32_t a01 = (it.acc * 0x00204081u) & 0x01010101u;   // bit q -> bit 8q
+    Bsm[p] = it.b ^ a01;
+    nacc += __popc(it.acc & vmask);
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        dE[q] += ((it.acc >> q) & 1u) ? 2 * ((int)((it.mb >> (8 * q)) & 0xFFu) - 128) : 0;
+    // field change of the neighbours: -2 x_q per accepted replica q
+    return ((a01 & ~it.smask) << 1) - ((a01 & it.smask) << 1);
+}
+
+// Per-warp ring of accepted items (position, D) awaiting their neighbour
+// updates; a full round gives every lane one item, so the row walks run with
+// all lanes busy instead of with the few lanes that happened to accept.
+constexpr int PK_QCAP = 64;   // backlog < 32 + 32 after each drain
+
+__device__ __forceinline__ void pk_enqueue(uint2 *__restrict__ Q, uint32_t &qtail, int p, uint32_t D,
+                                           int lane) {
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, D != 0u);
+    if (D) {
+        const uint32_t rank = __popc(bal & ((1u << lane) - 1u));
+        Q[(qtail + rank) & (PK_QCAP - 1)] = make_uint2((uint32_t)p, D);
+    }
+    qtail += __popc(bal);
+}
+
+template <bool WEIGHTED>
+__device__ __forceinline__ void pk_round(uint32_t *__restrict__ Bsm, const uint2 *__restrict__ Q,
+                                         uint32_t qhead, uint32_t count, const SweepArgs &a, int lane) {
+    __syncwarp();
+    if ((uint32_t)lane < count) {
+        const uint2 ent = Q[(qhead + lane) & (PK_QCAP - 1)];
+        const uint32_t D = ent.y;
+        const uint32_t e0 = __ldg(&a.g.prp[ent.x]), e1 = __ldg(&a.g.prp[ent.x + 1]);
+        for (uint32_t e = e0; e < e1; ++e) {
+            const uint2 v = __ldg(&a.g.pcol[e]);
+            const uint32_t idx[4] = {v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                if (WEIGHTED)
+                    atomicAdd(&Bsm[idx[t] & 0x7FFFu], (idx[t] & 0x8000u) ? 0u - D : D);
+                else
+                    atomicAdd(&Bsm[idx[t]], D);
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <bool WEIGHTED, int NTB, int MINB>
+__global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const bool act = !a.active || a.active[a.k];
+    const int nsweeps = act ? a.S : 0;
+    const int np = a.g.np;
+    uint32_t *Bsm = reinterpret_cast<uint32_t *>(smem);          // [np + 32], last 32 are scratch
+    uint32_t *T256 = Bsm + np + 32;                                 // [256] by m + 128
+    int32_t *cls = reinterpret_cast<int32_t *>(T256 + 256);
+    const int csz = (a.g.ncol + 1 + 3) & ~3;
+    int32_t *Eacc = cls + csz;      // [4]
+    int32_t *PS = Eacc + 4;         // [4]
+    int32_t *misc = PS + 4;         // best E, step, sweep, slot, copy-from (q+1), changed
+    uint32_t *Psm = reinterpret_cast<uint32_t *>(misc + 8);         // degree parity bits
+    const int npw = (np + 31) >> 5;
+    uint2 *Qall = reinterpret_cast<uint2 *>(Psm + ((npw + 1) & ~1));  // [NT/32][PK_QCAP]
+
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
+    uint2 *Q = Qall + (size_t)(tid >> 5) * PK_QCAP;
+    const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
+    for (int i = tid; i < 256; i += NT) {
+        const int m = i - 128;
+        T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
+    }
+    for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
+    for (int i = tid; i < npw; i += NT) Psm[i] = a.g.parity[i];
+
+    for (int blk = blockIdx.x; blk < a.nblk; blk += gridDim.x) {
+        const int slot0 = blk * 4;
+        if (tid < 4) PS[tid] = act ? a.parent[slot0 + tid] : slot0 + tid;
+        if (tid == 0) {
+            const int4 br = a.best_rec[blk];
+            misc[0] = br.x; misc[1] = br.y; misc[2] = br.z; misc[3] = br.w;
+            misc[4] = 0; misc[5] = 0;
+        }
+        __syncthreads();
+        if (tid < 4) Eacc[tid] = a.E_in[PS[tid]];
+        // Load: int8 spins + int16 fields of four replica rows -> packed bytes.
+        for (int c = tid; c < (np >> 2); c += NT) {
+            uint32_t w[4];
+            uint2 f[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const size_t row = (size_t)PS[q] * np + 4 * c;
+                w[q] = __ldg(reinterpret_cast<const uint32_t *>(a.spins_in + row));
+                f[q] = __ldg(reinterpret_cast<const uint2 *>(a.fields_in + row));
+            }
+            uint32_t o[4];
+            transpose4x4_bytes(w[0], w[1], w[2], w[3], o);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                uint32_t word = 0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t hv = j < 2 ? f[q].x : f[q].y;
+                    const uint32_t h128 = ((hv >> (16 * (j & 1))) + 128u) & 0xFFu;   // h + 128
+                    const uint32_t sbit = ((o[j] >> (8 * q)) & 0xFFu) == 1u ? 1u : 0u;
+                    word |= ((h128 & 0xFEu) | sbit) << (8 * q);
+                }
+                Bsm[4 * c + j] = word;
+            }
+        }
+        __syncthreads();
+
+        uint32_t vmask = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vmask |= (slot0 + q < a.R) ? (1u << q) : 0u;
+        const uint32_t c1 = (uint32_t)blk;
+        uint32_t nacc = 0;
+        for (int s = 0; s < nsweeps; ++s) {
+            const uint32_t c3 = TAG_SWEEP | (uint32_t)s;
+            int dE[4] = {0, 0, 0, 0};
+            for (int c = 0; c < a.g.ncol; ++c) {
+                const int p0 = cls[c], p1 = cls[c + 1];
+                uint32_t qhead = 0, qtail = 0;   // warp-uniform
+                for (int base = p0; base < p1; base += 2 * NT) {   // trip count uniform in the CTA
+                    const int pA = base + tid, pB = pA + NT;
+                    PkItem A, Bi;
+                    A.acc = 0;
+                    Bi.acc = 0;
+                    if (pA < p1) pk_decide(Bsm, T256, Psm, a, pA, c1, c3, A);
+                    if (pB < p1) pk_decide(Bsm, T256, Psm, a, pB, c1, c3, Bi);
+                    const uint32_t DA = pk_commit_self(Bsm, pA, A, vmask, dE, nacc);
+                    const uint32_t DB = pk_commit_self(Bsm, pB, Bi, vmask, dE, nacc);
+                    pk_enqueue(Q, qtail, pA, DA, lane);
+                    if (qtail - qhead >= 32u) {
+                        pk_round<WEIGHTED>(Bsm, Q, qhead, 32u, a, lane);
+                        qhead += 32u;
+                    }
+                    pk_enqueue(Q, qtail, pB, DB, lane);
+                    if (qtail - qhead >= 32u) {
+                        pk_round<WEIGHTED>(Bsm, Q, qhead, 32u, a, lane);
+                        qhead += 32u;
+                    }
+                }
+                if (qtail != qhead) pk_round<WEIGHTED>(Bsm, Q, qhead, qtail - qhead, a, lane);
+                __syncthreads();
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int v = __reduce_add_sync(0xFFFFFFFFu, dE[q]);
+                if (lane == 0 && v != 0) atomicAdd(&Eacc[q], v);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                int bq = -1, bE = 0x7FFFFFFF;
+                for (int q = 0; q < 4; ++q)
+                    if (slot0 + q < a.R && Eacc[q] < bE) { bE = Eacc[q]; bq = q; }
+                misc[4] = 0;
+                if (bq >= 0) {
+                    atomicMin(&a.sweep_emin[(size_t)a.k * a.S + s], bE);
+                    if (bE < misc[0]) {
+                        misc[0] = bE; misc[1] = a.k; misc[2] = s; misc[3] = slot0 + bq;
+                        misc[4] = bq + 1; misc[5] = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            if (misc[4]) {
+                const int sh = 8 * (misc[4] - 1);
+                uint32_t *dst = reinterpret_cast<uint32_t *>(a.best_cfg + (size_t)blk * np);
+                for (int c = tid; c < (np >> 2); c += NT) {
+                    uint32_t v = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t sb = (Bsm[4 * c + j] >> sh) & 1u;
+                        const bool real = 4 * c + j < a.g.n;
+                        v |= (real ? (sb ? 0x01u : 0xFFu) : 0u) << (8 * j);
+                    }
+                    dst[c] = v;
+                }
+                __syncthreads();
+            }
+        }
+        // Store: packed bytes -> int8 spins + int16 fields of the next buffers.
+        for (int c = tid; c < (np >> 2); c += NT) {
+            uint32_t sp[4] = {0u, 0u, 0u, 0u};
+            uint32_t fx[4] = {0u, 0u, 0u, 0u}, fy[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int p = 4 * c + j;
+                const uint32_t word = Bsm[p];
+                const uint32_t pb = (Psm[p >> 5] >> (p & 31)) & 1u;
+                const bool real = p < a.g.n;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t byte = (word >> (8 * q)) & 0xFFu;
+                    const uint32_t sv = real ? ((byte & 1u) ? 0x01u : 0xFFu) : 0u;
+                    const int h = real ? (int)((byte & 0xFEu) | pb) - 128 : 0;
+                    sp[q] |= sv << (8 * j);
+                    if (j < 2) fx[q] |= ((uint32_t)h & 0xFFFFu) << (16 * j);
+                    else fy[q] |= ((uint32_t)h & 0xFFFFu) << (16 * (j - 2));
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const size_t row = (size_t)(slot0 + q) * np + 4 * c;
+                *reinterpret_cast<uint32_t *>(a.spins_out + row) = sp[q];
+                *reinterpret_cast<uint2 *>(a.fields_out + row) = make_uint2(fx[q], fy[q]);
+            }
+        }
+        if (tid < 4) a.E_out[slot0 + tid] = Eacc[tid];
+        if (tid == 0 && misc[5]) a.best_rec[blk] = make_int4(misc[0], misc[1], misc[2], misc[3]);
+        const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, nacc);
+        if (act && lane == 0 && wsum) atomicAdd(&a.accepts[a.k], (unsigned long long)wsum);
+        __syncthreads();
+    }
+}
+
+template <bool W>
+void *packed_kernel(int threads) {
+    switch (threads) {
+        case 128: return reinterpret_cast<void *>(&k_sweep_packed<W, 128, 12>);
+        case 256: return reinterpret_cast<void *>(&k_sweep_packed<W, 256, 6>);
+        case 384: return reinterpret_cast<void *>(&k_sweep_packed<W, 384, 4>);
+        case 512: return reinterpret_cast<void *>(&k_sweep_packed<W, 512, 3>);
+        default: return reinterpret_cast<void *>(&k_sweep_packed<W, 1024, 1>);
+    }
+}
+
 template <int G, int FB, bool W>
 void *kernel_ptr() {
     return reinterpret_cast<void *>(&k_sweep<G, FB, W>);
 }
 
-void *select_kernel(int G, int fb, bool weighted) {
+void *select_kernel(int G, int fb, bool weighted, int threads) {
+    if (fb == 7) return weighted ? packed_kernel<true>(threads) : packed_kernel<false>(threads);
     if (G == 1) {
         if (fb == 16) return weighted ? kernel_ptr<1, 16, true>() : kernel_ptr<1, 16, false>();
         return weighted ? kernel_ptr<1, 8, true>() : kernel_ptr<1, 8, false>();
@@ -295,12 +568,19 @@ void *select_kernel(int G, int fb, bool weighted) {
 
 cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int threads,
                             bool weighted, SweepConfig *cfg) {
-    const int HW = field_bits == 16 ? 2 : 1;
-    size_t smem = (size_t)g.np * G * 4 * (1 + HW);
-    smem += (size_t)((g.mmax + 1 + 3) & ~3) * 4;
-    smem += (size_t)((g.ncol + 1 + 3) & ~3) * 4;
-    smem += (size_t)(8 * G + 8) * 4;
-    void *fn = select_kernel(G, field_bits, weighted);
+    size_t smem;
+    if (field_bits == 7) {
+        G = 1;
+        smem = (size_t)(g.np + 32) * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + 16 * 4 +
+               (size_t)((((g.np + 31) / 32) + 1) & ~1) * 4 + (size_t)(threads / 32) * PK_QCAP * 8;
+    } else {
+        const int HW = field_bits == 16 ? 2 : 1;
+        smem = (size_t)g.np * G * 4 * (1 + HW);
+        smem += (size_t)((g.mmax + 1 + 3) & ~3) * 4;
+        smem += (size_t)((g.ncol + 1 + 3) & ~3) * 4;
+        smem += (size_t)(8 * G + 8) * 4;
+    }
+    void *fn = select_kernel(G, field_bits, weighted, threads);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, occ = 0;
@@ -319,7 +599,7 @@ cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int
 }
 
 cudaError_t launch_sweep(const SweepConfig &cfg, const SweepArgs &a, cudaStream_t st) {
-    void *fn = select_kernel(cfg.G, cfg.field_bits, a.g.wt != nullptr);
+    void *fn = select_kernel(cfg.G, cfg.field_bits, a.g.wt != nullptr, cfg.threads);
     void *args[] = {const_cast<SweepArgs *>(&a)};
     return cudaLaunchKernel(fn, dim3(cfg.grid), dim3(cfg.threads), args, cfg.smem, st);
 }

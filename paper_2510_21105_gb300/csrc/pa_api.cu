@@ -115,7 +115,8 @@ struct pa_ctx {
     std::vector<uint32_t> rp_p;         // position-order CSR
     std::vector<uint16_t> col_p;
     std::vector<int8_t> w_p;
-    DevBuf d_rp, d_col, d_w, d_vid, d_cls, d_pos;
+    DevBuf d_rp, d_col, d_w, d_vid, d_cls, d_pos, d_parity, d_prp, d_pcol;
+    bool packed_ok = false;
     RunState run;
     std::string err;
     int64_t h2d = 0, d2h = 0;
@@ -131,6 +132,10 @@ struct pa_ctx {
         g.wt = weighted ? d_w.as<int8_t>() : nullptr;
         g.vid = d_vid.as<uint32_t>();
         g.cls = d_cls.as<int32_t>();
+        g.parity = d_parity.as<uint32_t>();
+        g.prp = d_prp.as<uint32_t>();
+        g.pcol = d_pcol.as<uint2>();
+        g.packed_ok = packed_ok ? 1 : 0;
         return g;
     }
 };
@@ -213,9 +218,12 @@ void collect_events(RunState &r) {
 
 int validate_opts(pa_ctx *c, const pa_anneal_opts &o) {
     if (o.variant < 0 || o.variant > 2) return fail(c, PA_EINVAL, "variant");
-    if (o.field_bits != 16 && o.field_bits != 8) return fail(c, PA_EINVAL, "field_bits must be 16 or 8");
-    if (o.field_bits == 8 && c->maxdeg > 127)
-        return fail(c, PA_EINVAL, "8-bit fields need max degree <= 127");
+    if (o.field_bits != 16 && o.field_bits != 8 && o.field_bits != 7)
+        return fail(c, PA_EINVAL, "field_bits must be 0, 16, 8 or 7");
+    if (o.field_bits != 16 && c->maxdeg > 127)
+        return fail(c, PA_EINVAL, "8- and 7-bit fields need max degree <= 127");
+    if (o.field_bits == 7 && !c->packed_ok)
+        return fail(c, PA_EINVAL, "the packed layout needs n <= 32720");
     if (o.nlm_period < 0) return fail(c, PA_EINVAL, "nlm_period < 0");
     if (o.replicas_per_cta != 0 && o.replicas_per_cta != 4 && o.replicas_per_cta != 8)
         return fail(c, PA_EINVAL, "replicas_per_cta must be 0, 4 or 8");
@@ -263,7 +271,7 @@ void pa_default_opts(pa_anneal_opts *o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->variant = PA_VARIANT_I8;
-    o->field_bits = 16;
+    o->field_bits = 0;
     o->rho = 0.5;
     o->adapt_J = 8;
     o->adapt_dbeta_max = 0.05;
@@ -370,7 +378,8 @@ int pa_create(pa_ctx **out, int32_t n, const uint32_t *row_ptr, const uint16_t *
     // Upload.
     if (!c->d_rp.alloc(sizeof(uint32_t) * (n + 1)) || !c->d_col.alloc(sizeof(uint16_t) * (m2 + 8)) ||
         !c->d_w.alloc(m2 + 16) || !c->d_vid.alloc(sizeof(uint32_t) * n) ||
-        !c->d_cls.alloc(sizeof(int32_t) * (ncol + 1)) || !c->d_pos.alloc(sizeof(int32_t) * n)) {
+        !c->d_cls.alloc(sizeof(int32_t) * (ncol + 1)) || !c->d_pos.alloc(sizeof(int32_t) * n) ||
+        !c->d_parity.alloc(sizeof(uint32_t) * ((c->np + 31) / 32))) {
         delete c;
         return PA_ENOMEM;
     }
@@ -385,6 +394,30 @@ int pa_create(pa_ctx **out, int32_t n, const uint32_t *row_ptr, const uint16_t *
         e1 = copy(c, c->d_cls.p, c->cls.data(), sizeof(int32_t) * (ncol + 1), cudaMemcpyHostToDevice);
     if (e1 == cudaSuccess)
         e1 = copy(c, c->d_pos.p, c->pos.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice);
+    c->packed_ok = c->np + 32 <= 32768;
+    if (e1 == cudaSuccess && c->packed_ok) {
+        std::vector<uint32_t> prp(n + 1, 0u);
+        for (int32_t p = 0; p < n; ++p) prp[p + 1] = prp[p] + (c->rp_p[p + 1] - c->rp_p[p] + 3) / 4;
+        std::vector<uint16_t> pcol((size_t)prp[n] * 4 + 4);
+        for (int32_t p = 0; p < n; ++p) {
+            size_t o = (size_t)prp[p] * 4;
+            for (uint32_t e = c->rp_p[p]; e < c->rp_p[p + 1]; ++e, ++o)
+                pcol[o] = (uint16_t)(c->col_p[e] | (c->w_p[e] < 0 ? 0x8000u : 0u));
+            for (; o < (size_t)prp[p + 1] * 4; ++o) pcol[o] = (uint16_t)(c->np + (p & 31));
+        }
+        if (!c->d_prp.alloc(4 * (size_t)(n + 1)) || !c->d_pcol.alloc(2 * pcol.size())) {
+            delete c;
+            return PA_ENOMEM;
+        }
+        e1 = copy(c, c->d_prp.p, prp.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice);
+        if (e1 == cudaSuccess) e1 = copy(c, c->d_pcol.p, pcol.data(), 2 * pcol.size(), cudaMemcpyHostToDevice);
+    }
+    if (e1 == cudaSuccess) {
+        std::vector<uint32_t> par((c->np + 31) / 32, 0u);
+        for (int32_t p = 0; p < n; ++p)
+            if ((c->rp_p[p + 1] - c->rp_p[p]) & 1u) par[p >> 5] |= 1u << (p & 31);
+        e1 = copy(c, c->d_parity.p, par.data(), sizeof(uint32_t) * par.size(), cudaMemcpyHostToDevice);
+    }
     if (e1 != cudaSuccess) {
         delete c;
         cudaGetLastError();
@@ -408,7 +441,7 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     pa_anneal_opts o;
     pa_default_opts(&o);
     if (opts) o = *opts;
-    if (o.field_bits == 0) o.field_bits = 16;
+    if (o.field_bits == 0) o.field_bits = (c->maxdeg <= 127 && c->packed_ok) ? 7 : 16;
     if (K < 0 || R < 1 || R > 65536 || sweeps < 0 || sweeps >= (1 << 28))
         return fail(c, PA_EINVAL, "K, R (1..65536) or sweeps out of range");
     if (int rc = validate_opts(c, o)) return rc;
@@ -438,11 +471,12 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     r.variant = PA_VARIANT_I8;
     // Sweep kernel shape.
     int G = o.replicas_per_cta == 8 ? 2 : 1;
-    int threads = o.threads_per_cta ? o.threads_per_cta : 512;
+    int threads = o.threads_per_cta ? o.threads_per_cta : (o.field_bits == 7 ? 128 : 512);
     pa::GraphDev g = c->gdev();
     cudaError_t ce = pa::sweep_configure(g, R, G, o.field_bits, threads, c->weighted, &r.sweep);
     if (ce != cudaSuccess && o.replicas_per_cta == 0 && G == 1) return cuda_fail(c, ce, "sweep_configure");
     if (ce != cudaSuccess) return cuda_fail(c, ce, "sweep_configure");
+    G = r.sweep.G;
     r.Rpad = ((R + 4 * G - 1) / (4 * G)) * 4 * G;
     r.nblk = r.Rpad / (4 * G);
     r.nch = (R + pa::RS_CHUNK - 1) / pa::RS_CHUNK;

@@ -54,6 +54,13 @@ struct GraphDev {
     const int8_t *wt;     // [2M] weights or nullptr (all +1)
     const uint32_t *vid;  // [n] original vertex of each position
     const int32_t *cls;   // [ncol+1] colour class boundaries in positions
+    const uint32_t *parity;  // [(np+31)/32] bit p = deg(p) & 1
+    // Rows padded to multiples of 4 entries for 8-byte loads (packed kernel):
+    // entry = neighbour position | 0x8000 if the weight is -1; padding entries
+    // point at one of 32 scratch words after the np real ones.
+    const uint32_t *prp;     // [n+1] row starts in units of 4 entries
+    const uint2 *pcol;       // [prp[n]] four 16-bit entries each
+    int32_t packed_ok;       // the padded encoding exists (np + 32 <= 32768)
 };
 
 struct SweepArgs {
@@ -108,7 +115,7 @@ cudaError_t launch_stamp(unsigned long long *stamp, cudaStream_t st);
 
 struct SweepConfig {
     int G;          // replica groups of 4 per CTA (1 or 2)
-    int field_bits; // 16 or 8
+    int field_bits; // 16, 8, or 7 (packed spin + field byte)
     int threads;
     int grid;
     size_t smem;

@@ -19,9 +19,9 @@ def _gpu():
     require_gpu()
 
 
-def _replay_check(g, betas, R, S, seed, k, subset, nlm_period=0):
+def _replay_check(g, betas, R, S, seed, k, subset, nlm_period=0, **opts):
     a = B.Annealer.from_graph(g)
-    a.begin(betas, R, S, seed, record_counts=1, nlm_period=nlm_period)
+    a.begin(betas, R, S, seed, record_counts=1, nlm_period=nlm_period, **opts)
     a.run(k)
     a.sync()
     spins_a, E_a = a.state()
@@ -42,12 +42,13 @@ def _replay_check(g, betas, R, S, seed, k, subset, nlm_period=0):
     return E_a
 
 
-def test_replay_g63like_full_population():
+@pytest.mark.parametrize("field_bits", [0, 16])
+def test_replay_g63like_full_population(field_bits):
     c = wl.CONFIGS["g63like"]
     g = c["graph"]()
     betas = wl.linear_betas(*c["beta"], c["K"])
     subset = np.array([0, 1, 2, 3, 4097, 8190, 12345, 16383])
-    _replay_check(g, betas, c["R"], c["S"], c["seed"], 3, subset)
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], 3, subset, field_bits=field_bits)
 
 
 def test_replay_g63like_nonlocal_step():

@@ -31,18 +31,29 @@ def test_tables_and_colouring_match_oracle():
     a.close()
 
 
-def test_parity_gnp800_full_workload():
+@pytest.mark.parametrize("field_bits", [0, 16])
+def test_parity_gnp800_full_workload(field_bits):
     # N = 800, p = 0.06, R = 256, beta 0.1 -> 3.0 in 100 steps, 4 sweeps, seed 0.
     c = wl.CONFIGS["gnp800"]
     g = c["graph"]()
     betas = wl.linear_betas(*c["beta"], c["K"])
-    gpu = run_gpu(g, betas, c["R"], c["S"], c["seed"])
-    orc = run_oracle(g, betas, c["R"], c["S"], c["seed"])
+    gpu = run_gpu(g, betas, c["R"], c["S"], c["seed"], field_bits=field_bits)
+    orc = _oracle_cached("gnp800", lambda: run_oracle(g, betas, c["R"], c["S"], c["seed"]))
     assert_parity(gpu, orc, g, c["R"], c["S"])
 
 
-@pytest.mark.parametrize("R,opts", [(6, {}), (13, {"field_bits": 8}), (1, {}),
-                                    (24, {"replicas_per_cta": 8}),
+_ORACLE_CACHE = {}
+
+
+def _oracle_cached(key, fn):
+    if key not in _ORACLE_CACHE:
+        _ORACLE_CACHE[key] = fn()
+    return _ORACLE_CACHE[key]
+
+
+@pytest.mark.parametrize("R,opts", [(6, {}), (6, {"field_bits": 16}), (13, {"field_bits": 8}),
+                                    (1, {}), (1, {"field_bits": 16}), (7, {"field_bits": 7, "threads_per_cta": 256}),
+                                    (24, {"replicas_per_cta": 8, "field_bits": 16}),
                                     (40, {"replicas_per_cta": 8, "field_bits": 8, "threads_per_cta": 128})])
 def test_parity_ragged_signed(R, opts):
     g = wl.from_edges(37, *_random_edges(37, 90, seed=R), name="ragged")
@@ -146,6 +157,8 @@ def test_repeat_runs_are_identical_and_launch_shape_free():
     betas = wl.linear_betas(0.2, 3.0, 6)
     r1 = run_gpu(g, betas, 64, 3, seed=77)
     r2 = run_gpu(g, betas, 64, 3, seed=77, threads_per_cta=256)
-    r3 = run_gpu(g, betas, 64, 3, seed=77, replicas_per_cta=8, threads_per_cta=1024)
-    for r in (r2, r3):
+    r3 = run_gpu(g, betas, 64, 3, seed=77, replicas_per_cta=8, threads_per_cta=1024, field_bits=16)
+    r4 = run_gpu(g, betas, 64, 3, seed=77, field_bits=8)
+    r5 = run_gpu(g, betas, 64, 3, seed=77, field_bits=16)
+    for r in (r2, r3, r4, r5):
         assert np.array_equal(r1["spins"], r["spins"]) and r1["best"] == r["best"]
