@@ -223,6 +223,51 @@ typedef void *(*pa_alloc_fn)(size_t bytes, void *user);
 typedef void (*pa_free_fn)(void *ptr, void *user);
 void pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_fn, void *user);
 
+/* ---------------------------------------------------------------------------
+ * Resampling step without any device allocation.
+ *
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory: code being recorded into a CUDA graph
+ * by stream capture, processes whose device-memory budget is owned by a host
+ * framework, and latency-critical loops that forbid allocator calls. It
+ * performs the same reweighting and systematic resampling as one temperature
+ * step of pa_anneal (weights exp(-(beta_k - beta_prev)(E_r - E_min)) as FP64
+ * products of squarings, pairwise-tree weight sum, integer weights
+ * floor(2^32 w_r), offset word from Philox(0, 0, k, tag 1) keyed by seed) and
+ * returns bit-identical copy counts and parents.
+ *
+ *   energies  device int32[R]: energies of the population entering step k
+ *   R         1..PA_NOALLOC_MAX_R (larger R returns PA_EINVAL)
+ *   beta_prev, beta_k   finite, 0 <= beta_prev <= beta_k (else PA_EINVAL)
+ *   seed, k   key and step index of the offset word
+ *   parent    device int32[R]: new slot s receives old slot parent[s]
+ *   counts    device int32[R] copy counts, or NULL
+ *   out       host result (weight sum A, integer total T, E_min, offset o),
+ *             or NULL; when given, the call waits for the stream
+ *   stream    cudaStream_t, NULL = legacy default stream
+ *
+ * Scratch lives in a fixed file-scope device array of about 0.6 MB that every
+ * GPU loading the library holds until the process exits; no cudaMalloc,
+ * cudaFree or allocating library routine is called. The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current, so make the first call on each device before any stream
+ * capture. All calls share the array and it keeps the last call's contents;
+ * calls that overlap on the GPU (other streams, other threads) race on it.
+ * Returns PA_OK, PA_EINVAL or PA_ECUDA.
+ */
+#define PA_NOALLOC_MAX_R 32768
+
+typedef struct {
+    double A;        /* FP64 weight sum */
+    uint64_t T;      /* sum of integer weights */
+    int32_t emin;    /* minimum energy */
+    uint32_t o;      /* systematic-resampling offset word */
+} pa_resample_result;
+
+int pa_resample_noalloc(const int32_t *energies, int32_t R, double beta_prev, double beta_k,
+                        uint64_t seed, int32_t k, int32_t *parent, int32_t *counts,
+                        pa_resample_result *out, void *stream);
+
 /* Text of an error code, and the detail of the last error on ctx. */
 const char *pa_strerror(int code);
 const char *pa_last_error(const pa_ctx *ctx);

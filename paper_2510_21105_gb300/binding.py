@@ -51,6 +51,10 @@ class pa_step_arrays(C.Structure):
                  "nlm_flips", "jsel", "counts")]
 
 
+class pa_resample_result(C.Structure):
+    _fields_ = [("A", C.c_double), ("T", C.c_uint64), ("emin", C.c_int32), ("o", C.c_uint32)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -91,6 +95,8 @@ def lib():
                 "pa_tables": ([vp, i32, vp, vp], C.c_int),
                 "pa_colouring": ([vp, vp, vp], C.c_int),
                 "pa_set_allocator": ([ALLOC_FN, FREE_FN, vp], None),
+                "pa_resample_noalloc": ([vp, i32, dbl, dbl, u64, i32, vp, vp, C.POINTER(pa_resample_result),
+                                         vp], C.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -105,7 +111,8 @@ def exported_symbols():
     return ["pa_version", "pa_strerror", "pa_last_error", "pa_default_opts", "pa_create",
             "pa_destroy", "pa_anneal", "pa_anneal_begin", "pa_anneal_run", "pa_sync", "pa_best",
             "pa_best_record", "pa_get_state", "pa_set_state", "pa_save", "pa_load", "pa_stats",
-            "pa_step_stats", "pa_tables", "pa_colouring", "pa_set_allocator", "pa_run_info"]
+            "pa_step_stats", "pa_tables", "pa_colouring", "pa_set_allocator", "pa_run_info",
+            "pa_resample_noalloc"]
 
 
 def strerror(code: int) -> str:
@@ -252,6 +259,18 @@ def pa_colouring(ctx, n: int):
     if rc < 0:
         _check(rc, "pa_colouring", ctx)
     return rc, colour, pos
+
+
+def pa_resample_noalloc(energies_ptr: int, R: int, beta_prev: float, beta_k: float, seed: int, k: int,
+                        parent_ptr: int, counts_ptr: int | None = None, stream=None):
+    """Resampling step with caller-owned device buffers and no device allocation
+    (see include/pa.h); pointers are raw device addresses."""
+    res = pa_resample_result()
+    _check(lib().pa_resample_noalloc(C.c_void_p(energies_ptr), int(R), float(beta_prev), float(beta_k),
+                                     int(seed) & (2**64 - 1), int(k), C.c_void_p(parent_ptr),
+                                     C.c_void_p(counts_ptr) if counts_ptr else None, C.byref(res),
+                                     stream), "pa_resample_noalloc")
+    return dict(A=res.A, T=res.T, emin=res.emin, o=res.o)
 
 
 _alloc_refs = None
