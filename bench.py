@@ -16,6 +16,7 @@ scaling; the harness barrier and the max-over-ranks time use torch.distributed.
 from __future__ import annotations
 
 import argparse
+import collections
 import json
 import os
 import statistics
@@ -42,6 +43,11 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="anneal", choices=["anneal", "batch", "serve"],
+                   help="anneal: the headline line; batch / serve: the batched and served workloads")
+    p.add_argument("--instances", type=int, default=64)
+    p.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of the served trace")
+    p.add_argument("--rate", type=float, default=20.0, help="mean arrivals per second")
     p.add_argument("--config", default="g63like")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -164,22 +170,28 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ ours ---
-def sweep_roofline(stats, attempts_per_launch, peaks, clocks):
-    """Roofline of the sweep kernel (dominant kernel): integer-ALU bound. The
-    algorithmic integer work per attempt is the Philox share fixed by the
-    bit-exact contract plus the Metropolis decision."""
-    ops_per_attempt = 20.0
-    lanes_per_sm = 64.0
+# DRAM bytes of one k_sweep_packed launch (128 threads) on this workload, from
+# profiles/sweep_packed_g63like.md; reported only when the same kernel runs.
+SWEEP_TRAFFIC = {("k_sweep_packed", 128): 334.719744e6 + 289.454080e6}
+OPS_PER_ATTEMPT = 20.0   # a quarter Philox4x32-10 block (15) + decision (4) + flip updates (~1)
+INT_LANES_PER_SM = 128   # ALU pipe (LOP3/IADD3) 64 + FMA pipe (IMAD) 64
+
+
+def sweep_roofline(stats, attempts_per_launch, peaks, kernel):
+    """Roofline of the sweep kernel (dominant kernel): integer-issue bound."""
     launches = max(stats["sweep_launches"], 1)
     t = stats["sweep_ms"] / launches / 1e3
     if t <= 0:
         return None
-    achieved = attempts_per_launch * ops_per_attempt / t / 1e12
-    peak = SMS * lanes_per_sm * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    achieved = attempts_per_launch * OPS_PER_ATTEMPT / t / 1e12
+    clk = peaks.get("sm_max_mhz", 2070.0)
+    peak = SMS * INT_LANES_PER_SM * clk * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": None,
-            "kernel": "k_sweep", "avg_launch_ms": t * 1e3,
-            "attempts_per_s_in_kernel": attempts_per_launch / t}
+            "frac": achieved / peak, "traffic": SWEEP_TRAFFIC.get(kernel),
+            "kernel": f"{kernel[0]}<{kernel[1]} threads>", "avg_launch_ms": t * 1e3,
+            "attempts_per_s_in_kernel": attempts_per_launch / t,
+            "peak_source": f"derived: {SMS} SMs x {INT_LANES_PER_SM} integer lanes x {clk:.0f} MHz",
+            "smem_frac": attempts_per_launch * 6.6 / t / (SMS * 128 * clk * 1e6)}
 
 
 def run_ours(args, rank, world, dist):
@@ -245,7 +257,9 @@ def run_ours(args, rank, world, dist):
         ms_max = float(tt.item())
     value = world * attempts / (ms_max / 1e3)
     clocks = clk.summary()
-    roof = sweep_roofline(stats_acc, g.n * R * S, peaks, clocks)
+    kname = {7: "k_sweep_packed", 8: "k_sweep", 16: "k_sweep"}.get(layout_bits, "k_sweep")
+    kthreads = args.threads or (128 if layout_bits == 7 else 512)
+    roof = sweep_roofline(stats_acc, g.n * R * S, peaks, (kname, kthreads))
     ann.close()
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the region
@@ -290,8 +304,6 @@ def run_ours(args, rank, world, dist):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_sample(args.config, args.cpu_seconds)
-    if roof is not None:
-        roof["peak_source"] = f"derived: {SMS} SMs x 64 INT32 lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int8/int16 spins+fields, fp64 weights",
@@ -310,8 +322,149 @@ def run_ours(args, rank, world, dist):
     return 0
 
 
+# -------------------------------------------------------------- batched ---
+def run_batch(args):
+    """64 mixed instances (N ~ U[800, 20000]; random p = 12/(N-1), signed torus,
+    Delaunay; R cycling 1024/4096/16384), beta 0.1 -> 3.0 in 200 steps, 4 sweeps:
+    each instance annealed alone in turn (plain) vs all in one batched launch
+    captured in a CUDA graph; kernel shapes from the autotuner."""
+    import tempfile
+
+    import torch
+
+    from paper_2510_21105_gb300 import autotune
+    from paper_2510_21105_gb300 import binding as B
+    from paper_2510_21105_gb300 import build as build_mod
+    from paper_2510_21105_gb300 import workloads as wl
+
+    build_mod.build()
+    torch.cuda.set_device(0)
+    K, S = 200, 4
+    betas = wl.linear_betas(0.1, 3.0, K)
+    inst = wl.batch_instances(args.instances, seed=0)
+    cache = os.path.join(tempfile.gettempdir(), "pa_autotune_cache.json")
+    t0 = time.perf_counter()
+    opts = []
+    for i, it in enumerate(inst):
+        g = it["graph"]
+        cand = [c for c in autotune.CANDIDATES if c.get("variant") == 1 or c.get("field_bits") == 7]
+        o, _ = autotune.tune(g, betas, it["R"], S, seed=it["seed"], steps=1, cache_path=cache, candidates=cand)
+        opts.append(o)
+    tune_s = time.perf_counter() - t0
+    attempts = sum(it["graph"].n * it["R"] * S * K for it in inst)
+    anns = [B.Annealer.from_graph(it["graph"]) for it in inst]
+    # plain: one instance after another, each its own pa_anneal
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ann0 = anns[0]
+    ann0.anneal(betas, inst[0]["R"], S, inst[0]["seed"], **opts[0])   # warm-up
+    torch.cuda.synchronize()
+    ev0.record()
+    plain_best = []
+    for ann, it, o in zip(anns, inst, opts):
+        ann.anneal(betas, it["R"], S, it["seed"], **o)
+        plain_best.append(ann.best_record())
+    ev1.record()
+    torch.cuda.synchronize()
+    plain_ms = ev0.elapsed_time(ev1)
+    items = [(ann, betas, it["R"], S, it["seed"], K, o) for ann, it, o in zip(anns, inst, opts)]
+    B.pa_batch_anneal(items, n_streams=16, use_graph=True)   # warm-up (and graph build)
+    times = [B.pa_batch_anneal(items, n_streams=16, use_graph=True) for _ in range(max(args.steps, 1))]
+    batch_ms = statistics.median(times)
+    same = all(ann.best_record() == b for ann, b in zip(anns, plain_best))
+    for a in anns:
+        a.close()
+    line = {"mode": "batch", "metric": "batched attempts/s (64 mixed instances) vs plain one-instance-per-launch",
+            "value": attempts / (batch_ms / 1e3), "unit": UNIT, "plain_value": attempts / (plain_ms / 1e3),
+            "ratio": plain_ms / batch_ms, "batch_ms": batch_ms, "plain_ms": plain_ms,
+            "bit_identical_to_plain": same, "instances": len(inst), "attempts": attempts,
+            "autotune_s": tune_s,
+            "layouts": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts)),
+            "config": {"workload": "N~U[800,20000] random(p=12/(N-1))/torus/Delaunay, R 1024/4096/16384, "
+                                   "beta 0.1->3.0 K=200 S=4", "use_graph": True, "n_streams": 16}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- served ---
+def _serve_trace(seconds, rate, seed=1):
+    """Poisson arrivals; requests on random (p = 12/(N-1)) or signed torus
+    graphs, N ~ U[800, 20000], R = round(2^U[10, 15]), beta 0.1 -> 3.0 in 200
+    steps, 4 sweeps. A pool of 24 graphs is generated up front."""
+    from paper_2510_21105_gb300 import workloads as wl
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pool = []
+    for t in range(24):
+        n = int(rng.integers(800, 20001))
+        pool.append(wl.gnp_sparse(n, 12.0 / (n - 1), seed=5000 + t) if t % 2 == 0
+                    else wl.torus(int(round(np.sqrt(n))), seed=5000 + t))
+    trace, t = [], 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t > seconds:
+            break
+        trace.append((t, pool[int(rng.integers(0, len(pool)))], int(round(2 ** rng.uniform(10, 15))),
+                      len(trace)))
+    return trace
+
+
+def _serve(trace, betas, slots):
+    from paper_2510_21105_gb300 import binding as B
+
+    with B.Server(200 << 30, n_streams=slots, steps_per_tick=8) as srv:
+        ids = []
+        t0 = time.perf_counter()
+        for at, g, R, seed in trace:
+            delay = at - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(g, betas, R, 4, seed))
+        res = {}
+        while len(res) < len(ids):
+            for rid in ids:
+                if rid not in res and srv.poll(rid) not in (0, 1):
+                    res[rid] = srv.result(rid, config=False)
+            time.sleep(0.002)
+        makespan = time.perf_counter() - t0
+    out = [res[r] for r in ids]
+    lat = np.array([r["finish_ms"] - r["submit_ms"] for r in out])
+    att = sum(r["attempts"] for r in out)
+    return dict(p50_ms=float(np.percentile(lat, 50)), p99_ms=float(np.percentile(lat, 99)),
+                attempts_per_s=att / makespan, makespan_s=makespan,
+                best=[(r["energy"], r["step"], r["sweep"], r["slot"]) for r in out])
+
+
+def run_serve(args):
+    import torch
+
+    from paper_2510_21105_gb300 import build as build_mod
+    from paper_2510_21105_gb300 import workloads as wl
+
+    build_mod.build()
+    torch.cuda.set_device(0)
+    betas = wl.linear_betas(0.1, 3.0, 200)
+    trace = _serve_trace(args.serve_seconds, args.rate)
+    served = _serve(trace, betas, slots=16)
+    plain = _serve(trace, betas, slots=1)
+    line = {"mode": "serve", "metric": "served attempts/s with continuous batching vs plain one-at-a-time",
+            "value": served["attempts_per_s"], "unit": UNIT, "plain_value": plain["attempts_per_s"],
+            "ratio": served["attempts_per_s"] / plain["attempts_per_s"],
+            "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"],
+            "plain_p50_ms": plain["p50_ms"], "plain_p99_ms": plain["p99_ms"],
+            "requests": len(trace), "bit_identical_to_plain": served["best"] == plain["best"],
+            "config": {"workload": f"Poisson {args.rate}/s over {args.serve_seconds} s; random/torus N~U[800,20000]; "
+                                   "R=round(2^U[10,15]); beta 0.1->3.0 K=200 S=4", "slots": 16,
+                       "hbm_budget_gb": 200, "steps_per_tick": 8}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.mode == "batch":
+        return run_batch(args)
+    if args.mode == "serve":
+        return run_serve(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

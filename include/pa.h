@@ -203,6 +203,90 @@ int pa_stats(pa_ctx *ctx, pa_stats_t *out);
 /* Per-step records (waits for pending work). */
 int pa_step_stats(pa_ctx *ctx, pa_step_arrays *out);
 
+/* ---------------------------------------------------------------------------
+ * Batched anneals: many instances (each its own pa_ctx) advance through their
+ * temperature steps together. Step k of every job is enqueued before step
+ * k+1 of any, round-robin over n_streams streams, so instances of uneven size
+ * overlap on the device; with use_graph the whole multi-stream sequence is
+ * captured into one CUDA graph and launched once. Each job's results are
+ * read afterwards from its context (pa_best, pa_stats, ...) and are
+ * bit-identical to the same job run alone with pa_anneal (all randomness is
+ * keyed by seed, slot, step, sweep and vertex, never by scheduling).
+ */
+typedef struct {
+    pa_ctx *ctx;              /* from pa_create; owned by the caller */
+    const double *betas;      /* host, K entries (NULL in adaptive mode) */
+    int32_t K, R, sweeps;
+    uint64_t seed;
+    pa_anneal_opts opts;      /* per-job options; opts.stream is ignored */
+} pa_job;
+
+typedef struct {
+    int32_t n_streams;        /* 1..64; 0 = min(n_jobs, 16) */
+    int32_t use_graph;        /* 1 = capture into one CUDA graph, launch once */
+    void *stream;             /* origin stream; NULL = legacy default stream */
+} pa_batch_opts;
+
+/* Run all jobs to completion. elapsed_ms (may be NULL) receives the device
+ * time from the first step to the last (CUDA events on the origin stream;
+ * graph instantiation excluded). Errors: PA_EINVAL, PA_ENOMEM, PA_ECUDA (the
+ * failing job's pa_last_error gives the detail). */
+int pa_batch_anneal(const pa_job *jobs, int32_t n_jobs, const pa_batch_opts *opts, double *elapsed_ms);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a background thread admits anneal requests as device memory frees
+ * up (FIFO; admitted when the estimated footprint fits under the HBM budget
+ * and fewer than n_streams requests run, or when nothing else runs), keeps
+ * their populations resident, and advances every admitted request, each on
+ * its own stream, by steps_per_tick temperature steps per tick, so requests
+ * that arrive while others run overlap with them on the device (continuous
+ * batching). Each result is bit-identical to
+ * the same request run alone with pa_anneal. Times are host milliseconds
+ * since pa_server_start.
+ */
+typedef struct pa_server pa_server;
+
+typedef struct {
+    int32_t n;                /* graph as in pa_create (host arrays, copied */
+    const uint32_t *row_ptr;  /* by pa_server_submit) */
+    const uint16_t *col;
+    const int8_t *w;
+    const double *betas;      /* host, K entries (copied) */
+    int32_t K, R, sweeps;
+    uint64_t seed;
+    pa_anneal_opts opts;      /* opts.stream is ignored */
+} pa_request;
+
+typedef struct {
+    int64_t cut;              /* best cut (W - E*) / 2 */
+    int32_t energy, step, sweep, slot;
+    int32_t status;           /* PA_OK or the error of the request */
+    int64_t attempts;         /* spin-flip attempts performed */
+    double submit_ms, start_ms, finish_ms;
+} pa_response;
+
+typedef struct {
+    int64_t submitted, admitted, completed, queued, running;
+    int64_t bytes_in_use;     /* estimated device bytes of admitted requests */
+    int64_t attempts;         /* attempts of completed requests */
+    double elapsed_ms;
+} pa_server_stats_t;
+
+/* Start the server on the current device. hbm_budget_bytes > 0; n_streams
+ * = maximum concurrently running requests, 0..64 (0 = 16); steps_per_tick
+ * >= 0 (0 = 8). */
+int pa_server_start(pa_server **out, size_t hbm_budget_bytes, int32_t n_streams, int32_t steps_per_tick);
+/* Queue a request (inputs are copied; returns at once). */
+int pa_server_submit(pa_server *s, const pa_request *req, uint64_t *id);
+/* state: 0 queued, 1 running, 2 done, negative = failed with that error. */
+int pa_server_poll(pa_server *s, uint64_t id, int32_t *state);
+/* Result of a finished request (config: host int8[n] or NULL). PA_EBUSY if
+ * it has not finished. */
+int pa_server_result(pa_server *s, uint64_t id, pa_response *out, int8_t *config);
+int pa_server_stats(pa_server *s, pa_server_stats_t *out);
+/* Finish all submitted requests, then stop the thread and free everything. */
+int pa_server_stop(pa_server *s);
+
 /* Host-side copies of the tables the device uses for step k: the 32-bit
  * acceptance thresholds T[0..max_degree] and the 32 squarings q^(2^b) of
  * q = exp(-(beta_k - beta_{k-1})) used for the resampling weights. Either

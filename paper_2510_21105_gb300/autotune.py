@@ -1,0 +1,79 @@
+"""Per-instance autotuner for the sweep kernel.
+
+Candidates are the kernel shapes the library offers: the spin encoding (packed
+byte of spin + 7-bit field, int8 spin + int8 or int16 field, multi-spin coded
+32 replicas per word), the replicas per CTA (4 or 8 for the int8/int16
+layouts) and the threads per CTA (the colour-block width: positions of one
+colour updated in parallel per pass). Each feasible candidate anneals a
+short slice of the instance's own schedule (from its middle, where the
+acceptance rate is typical of most of a run) with per-launch CUDA-event
+timing; the fastest is kept. Results are bit-identical for every candidate,
+so tuning changes speed only. Choices are cached per instance shape
+(n, m, max degree, colours, weighted, R, S) in a JSON file.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+from . import binding as B
+
+CANDIDATES = [
+    dict(variant=0, field_bits=7, threads_per_cta=128),
+    dict(variant=0, field_bits=7, threads_per_cta=256),
+    dict(variant=0, field_bits=7, threads_per_cta=512),
+    dict(variant=0, field_bits=8, threads_per_cta=256),
+    dict(variant=0, field_bits=16, threads_per_cta=512),
+    dict(variant=0, field_bits=16, threads_per_cta=512, replicas_per_cta=8),
+    dict(variant=1, threads_per_cta=256),
+    dict(variant=1, threads_per_cta=128),
+]
+
+
+def feasible(g, cand) -> bool:
+    fb = cand.get("field_bits", 0)
+    if cand.get("variant") == 1:
+        return g.maxdeg <= 127
+    if fb in (7, 8) and g.maxdeg > 127:
+        return False
+    if fb == 7 and g.n > 32720:
+        return False
+    return True
+
+
+def shape_key(g, R, S) -> str:
+    return f"n{g.n}_m{g.m}_d{g.maxdeg}_w{int(g.w is not None)}_R{R}_S{S}"
+
+
+def tune(g, betas, R, S, seed=0, steps=2, cache_path=None, candidates=None):
+    """Return (best option dict, {candidate index: ms per sweep launch})."""
+    cache = {}
+    key = shape_key(g, R, S)
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+        if key in cache:
+            return cache[key]["opts"], cache[key]["times"]
+    cands = [c for c in (candidates or CANDIDATES) if feasible(g, c)]
+    mid = max(0, len(betas) // 2 - steps)
+    sl = list(betas[mid:mid + steps + 1])
+    times = {}
+    with B.Annealer.from_graph(g) as a:
+        for i, cand in enumerate(cands):
+            try:
+                a.begin(sl, R, S, seed, time_kernels=1, **cand)
+                a.run(len(sl))
+                a.sync()
+                st = a.stats()
+                times[i] = st["sweep_ms"] / max(st["sweep_launches"], 1)
+            except B.PaError:
+                continue
+    best = min(times, key=times.get)
+    out = (cands[best], {str(i): t for i, t in times.items()})
+    if cache_path:
+        cache[key] = {"opts": out[0], "times": out[1]}
+        tmp = cache_path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, cache_path)
+    return out

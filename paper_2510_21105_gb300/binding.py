@@ -51,6 +51,33 @@ class pa_step_arrays(C.Structure):
                  "nlm_flips", "jsel", "counts")]
 
 
+class pa_job(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("betas", C.c_void_p), ("K", C.c_int32), ("R", C.c_int32),
+                ("sweeps", C.c_int32), ("seed", C.c_uint64), ("opts", pa_anneal_opts)]
+
+
+class pa_batch_opts(C.Structure):
+    _fields_ = [("n_streams", C.c_int32), ("use_graph", C.c_int32), ("stream", C.c_void_p)]
+
+
+class pa_request(C.Structure):
+    _fields_ = [("n", C.c_int32), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("w", C.c_void_p),
+                ("betas", C.c_void_p), ("K", C.c_int32), ("R", C.c_int32), ("sweeps", C.c_int32),
+                ("seed", C.c_uint64), ("opts", pa_anneal_opts)]
+
+
+class pa_response(C.Structure):
+    _fields_ = [("cut", C.c_int64), ("energy", C.c_int32), ("step", C.c_int32), ("sweep", C.c_int32),
+                ("slot", C.c_int32), ("status", C.c_int32), ("attempts", C.c_int64),
+                ("submit_ms", C.c_double), ("start_ms", C.c_double), ("finish_ms", C.c_double)]
+
+
+class pa_server_stats_t(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("admitted", C.c_int64), ("completed", C.c_int64),
+                ("queued", C.c_int64), ("running", C.c_int64), ("bytes_in_use", C.c_int64),
+                ("attempts", C.c_int64), ("elapsed_ms", C.c_double)]
+
+
 class pa_resample_result(C.Structure):
     _fields_ = [("A", C.c_double), ("T", C.c_uint64), ("emin", C.c_int32), ("o", C.c_uint32)]
 
@@ -97,6 +124,13 @@ def lib():
                 "pa_set_allocator": ([ALLOC_FN, FREE_FN, vp], None),
                 "pa_resample_noalloc": ([vp, i32, dbl, dbl, u64, i32, vp, vp, C.POINTER(pa_resample_result),
                                          vp], C.c_int),
+                "pa_batch_anneal": ([C.POINTER(pa_job), i32, C.POINTER(pa_batch_opts), C.POINTER(dbl)], C.c_int),
+                "pa_server_start": ([C.POINTER(vp), C.c_size_t, i32, i32], C.c_int),
+                "pa_server_submit": ([vp, C.POINTER(pa_request), C.POINTER(u64)], C.c_int),
+                "pa_server_poll": ([vp, u64, C.POINTER(i32)], C.c_int),
+                "pa_server_result": ([vp, u64, C.POINTER(pa_response), vp], C.c_int),
+                "pa_server_stats": ([vp, C.POINTER(pa_server_stats_t)], C.c_int),
+                "pa_server_stop": ([vp], C.c_int),
             }
             for name, (args, res) in sig.items():
                 fn = getattr(L, name)
@@ -112,7 +146,8 @@ def exported_symbols():
             "pa_destroy", "pa_anneal", "pa_anneal_begin", "pa_anneal_run", "pa_sync", "pa_best",
             "pa_best_record", "pa_get_state", "pa_set_state", "pa_save", "pa_load", "pa_stats",
             "pa_step_stats", "pa_tables", "pa_colouring", "pa_set_allocator", "pa_run_info",
-            "pa_resample_noalloc"]
+            "pa_resample_noalloc", "pa_batch_anneal", "pa_server_start", "pa_server_submit",
+            "pa_server_poll", "pa_server_result", "pa_server_stats", "pa_server_stop"]
 
 
 def strerror(code: int) -> str:
@@ -271,6 +306,91 @@ def pa_resample_noalloc(energies_ptr: int, R: int, beta_prev: float, beta_k: flo
                                      C.c_void_p(counts_ptr) if counts_ptr else None, C.byref(res),
                                      stream), "pa_resample_noalloc")
     return dict(A=res.A, T=res.T, emin=res.emin, o=res.o)
+
+
+def pa_batch_anneal(items, n_streams: int = 0, use_graph: bool = False, stream=None) -> float:
+    """Run many anneals together (see include/pa.h). items: list of
+    (Annealer, betas, R, S, seed, K, opts-dict). Returns the device time in ms."""
+    arr = (pa_job * len(items))()
+    keep = []
+    for i, (ann, betas, R, S, seed, K, kw) in enumerate(items):
+        b = _betas(betas)
+        keep.append(b)
+        K = len(b) if (K is None and b is not None) else K
+        o = pa_default_opts(**(kw or {}))
+        arr[i] = pa_job(ann.ctx, None if b is None else b.ctypes.data, int(K), int(R), int(S),
+                        int(seed) & (2**64 - 1), o)
+        ann.R, ann.S, ann.K = R, S, K
+    bo = pa_batch_opts(int(n_streams), int(bool(use_graph)), stream)
+    ms = C.c_double(0.0)
+    rc = lib().pa_batch_anneal(arr, len(items), C.byref(bo), C.byref(ms))
+    if rc != PA_OK:
+        detail = ""
+        for ann, *_ in items:
+            d = lib().pa_last_error(ann.ctx).decode()
+            if d:
+                detail = d
+                break
+        raise PaError(rc, "pa_batch_anneal", detail)
+    return ms.value
+
+
+class Server:
+    """Continuous-batching request loop (pa_server_*): submit anneal requests,
+    poll, and read results; device memory is admitted against hbm_budget."""
+
+    def __init__(self, hbm_budget: int, n_streams: int = 16, steps_per_tick: int = 8):
+        self.h = C.c_void_p()
+        _check(lib().pa_server_start(C.byref(self.h), int(hbm_budget), int(n_streams), int(steps_per_tick)),
+               "pa_server_start")
+        self.n = {}
+
+    def submit(self, g, betas, R: int, S: int, seed: int, K: int | None = None, **opts) -> int:
+        rp = g.rp_u32
+        col = g.col_u16
+        w = None if g.w is None else np.ascontiguousarray(g.w, np.int8)
+        b = _betas(betas)
+        if K is None:
+            K = len(b) if b is not None else 0
+        req = pa_request(int(g.n), rp.ctypes.data, col.ctypes.data if len(col) else None,
+                         None if w is None else w.ctypes.data, None if b is None else b.ctypes.data,
+                         int(K), int(R), int(S), int(seed) & (2**64 - 1), pa_default_opts(**opts))
+        rid = C.c_uint64()
+        _check(lib().pa_server_submit(self.h, C.byref(req), C.byref(rid)), "pa_server_submit")
+        self.n[rid.value] = g.n
+        return rid.value
+
+    def poll(self, rid: int) -> int:
+        st = C.c_int32()
+        _check(lib().pa_server_poll(self.h, int(rid), C.byref(st)), "pa_server_poll")
+        return st.value
+
+    def result(self, rid: int, config: bool = True):
+        r = pa_response()
+        cfg = np.zeros(self.n[rid], np.int8) if config else None
+        rc = lib().pa_server_result(self.h, int(rid), C.byref(r), _ptr(cfg))
+        if rc == PA_EBUSY:
+            return None
+        _check(rc, "pa_server_result")
+        out = {name: getattr(r, name) for name, _ in pa_response._fields_}
+        out["config"] = cfg
+        return out
+
+    def stats(self) -> dict:
+        st = pa_server_stats_t()
+        _check(lib().pa_server_stats(self.h, C.byref(st)), "pa_server_stats")
+        return {name: getattr(st, name) for name, _ in pa_server_stats_t._fields_}
+
+    def stop(self):
+        if self.h:
+            _check(lib().pa_server_stop(self.h), "pa_server_stop")
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.stop()
 
 
 _alloc_refs = None

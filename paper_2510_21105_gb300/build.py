@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpa.so")
-SOURCES = ["pa_api.cu", "k_sweep.cu", "k_resample.cu", "k_moves.cu", "pa_noalloc.cu"]
+SOURCES = ["pa_api.cu", "k_sweep.cu", "k_resample.cu", "k_moves.cu", "pa_noalloc.cu", "pa_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -67,7 +67,7 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"]
+    cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart", "-lpthread"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

@@ -1,6 +1,8 @@
 // k_moves.cu -- Houdayer non-local moves and ESS-adaptive temperature steps
 // (Sec. 3 of arXiv 2510.21105 names both without defining them; the rules
 // implemented here are the library's readings, stated in pa_moves.cuh).
+#include <mutex>
+
 #include "pa_moves.cuh"
 
 namespace pa {
@@ -321,8 +323,16 @@ cudaError_t launch_nonlocal(const NlmArgs &a, void *scratch, cudaStream_t st, in
     *launches = 2;
     if (a.R >= 2) {
         const size_t smem = nlm_smem_bytes(a.g.np);
-        cudaError_t e = cudaFuncSetAttribute(k_nlm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        static std::mutex mu;
+        static size_t raised = 0;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            if (smem > raised) {   // per-function attribute: only ever raise it
+                cudaError_t e = cudaFuncSetAttribute(k_nlm_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                raised = smem;
+            }
+        }
         k_nlm_pair<<<a.R / 2, 256, smem, st>>>(a, order);
         *launches = 3;
     }

@@ -17,6 +17,9 @@
 // sweep)) belongs to slot 4*(slot/4) + q.
 // The block is loaded from the parents chosen by the resampling (the copy of
 // the resampling is fused into this load) and written to the next buffers.
+#include <mutex>
+#include <unordered_map>
+
 #include "pa_internal.cuh"
 
 namespace pa {
@@ -538,6 +541,175 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Multi-spin-coded variant: W[p] holds the spins of 32 replicas (slots
+// 32*blk .. 32*blk+31) at position p, bit r = 1 for +1. No fields are kept:
+// an item (p, word) XORs its word with each neighbour's word (and with all
+// ones for a -1 weight), so bit r of d_j is 1 iff the bond (p, j) contributes
+// +1 to m_r = -x_p h_p; a bit-sliced counter over the neighbours gives c_r and
+// m_r = 2 c_r - deg(p). Groups of four replicas are spread to bytes and
+// decided exactly like the packed layout (same thresholds, same Philox word
+// (vertex, slot/4, step, sweep)). Accepted replicas flip with one XOR.
+__device__ __forceinline__ uint32_t spread_nibble(uint32_t nib) {   // bit q -> bit 8q
+    return (nib * 0x00204081u) & 0x01010101u;
+}
+
+template <int NPL, bool WEIGHTED, int NTB, int MINB>
+__global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const bool act = !a.active || a.active[a.k];
+    const int nsweeps = act ? a.S : 0;
+    const int np = a.g.np, n = a.g.n;
+    uint32_t *Wsm = reinterpret_cast<uint32_t *>(smem);           // [np]
+    uint32_t *T256 = Wsm + np;                                      // [256] by m + 128
+    int32_t *cls = reinterpret_cast<int32_t *>(T256 + 256);
+    const int csz = (a.g.ncol + 1 + 3) & ~3;
+    int32_t *Eacc = cls + csz;      // [32]
+    int32_t *PS = Eacc + 32;        // [32]
+    int32_t *misc = PS + 32;        // best E, step, sweep, slot, copy-from (r+1), changed
+
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
+    const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
+    for (int i = tid; i < 256; i += NT) {
+        const int m = i - 128;
+        T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
+    }
+    for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
+
+    for (int blk = blockIdx.x; blk < a.nblk; blk += gridDim.x) {
+        const int slot0 = blk * 32;
+        if (tid < 32) PS[tid] = act ? a.parent[slot0 + tid] : slot0 + tid;
+        if (tid == 0) {
+            const int4 br = a.best_rec[blk];
+            misc[0] = br.x; misc[1] = br.y; misc[2] = br.z; misc[3] = br.w;
+            misc[4] = 0; misc[5] = 0;
+        }
+        __syncthreads();
+        if (tid < 32) Eacc[tid] = a.E_in[PS[tid]];
+        // Load: 32 int8 spin rows -> one bit word per position.
+        for (int c = tid; c < (np >> 2); c += NT) {
+            uint32_t w4[4] = {0u, 0u, 0u, 0u};
+            for (int r = 0; r < 32; ++r) {
+                const uint32_t v = __ldg(reinterpret_cast<const uint32_t *>(a.spins_in + (size_t)PS[r] * np + 4 * c));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w4[j] |= ((((v >> (8 * j)) & 0xFFu) == 1u) ? 1u : 0u) << r;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Wsm[4 * c + j] = w4[j];
+        }
+        __syncthreads();
+        uint32_t vmask = 0xFFFFFFFFu;
+        if (slot0 + 32 > a.R) vmask = a.R > slot0 ? (0xFFFFFFFFu >> (32 - (a.R - slot0))) : 0u;
+        uint32_t nacc = 0;
+        for (int s = 0; s < nsweeps; ++s) {
+            const uint32_t c3 = TAG_SWEEP | (uint32_t)s;
+            for (int c = 0; c < a.g.ncol; ++c) {
+                const int p1 = cls[c + 1];
+                for (int p = cls[c] + tid; p < p1; p += NT) {
+                    const uint32_t e0 = __ldg(&a.g.rp[p]), e1 = __ldg(&a.g.rp[p + 1]);
+                    const uint32_t x = Wsm[p];
+                    const uint32_t vid = __ldg(&a.g.vid[p]);
+                    uint32_t pl[NPL];
+#pragma unroll
+                    for (int b = 0; b < NPL; ++b) pl[b] = 0u;
+                    for (uint32_t e = e0; e < e1; ++e) {
+                        uint32_t d = x ^ Wsm[__ldg(&a.g.col[e])];
+                        if (WEIGHTED && __ldg(&a.g.wt[e]) < 0) d = ~d;
+#pragma unroll
+                        for (int b = 0; b < NPL; ++b) {   // ripple-carry add of one bit per replica
+                            const uint32_t carry = pl[b] & d;
+                            pl[b] ^= d;
+                            d = carry;
+                        }
+                    }
+                    const uint32_t base = 128u - (e1 - e0);   // mb = 2c + 128 - deg
+                    uint32_t acc32 = 0;
+#pragma unroll 2
+                    for (int g = 0; g < 8; ++g) {
+                        uint32_t cb = 0;
+#pragma unroll
+                        for (int b = 0; b < NPL; ++b) cb |= spread_nibble((pl[b] >> (4 * g)) & 0xFu) << b;
+                        const uint32_t mb = (cb << 1) + base * 0x01010101u;
+                        const uint4 u = philox10(make_uint4(vid, (uint32_t)(blk * 8 + g), (uint32_t)a.k, c3),
+                                                 a.key0, a.key1);
+                        const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
+                            if ((idx <= 128u) | (uu[q] < T256[idx])) {
+                                acc32 |= 1u << (4 * g + q);
+                                atomicAdd(&Eacc[4 * g + q], 2 * ((int)idx - 128));
+                            }
+                        }
+                    }
+                    if (acc32) {
+                        Wsm[p] = x ^ acc32;
+                        nacc += __popc(acc32 & vmask);
+                    }
+                }
+                __syncthreads();
+            }
+            if (tid == 0) {
+                int bq = -1, bE = 0x7FFFFFFF;
+                for (int q = 0; q < 32; ++q)
+                    if (slot0 + q < a.R && Eacc[q] < bE) { bE = Eacc[q]; bq = q; }
+                misc[4] = 0;
+                if (bq >= 0) {
+                    atomicMin(&a.sweep_emin[(size_t)a.k * a.S + s], bE);
+                    if (bE < misc[0]) {
+                        misc[0] = bE; misc[1] = a.k; misc[2] = s; misc[3] = slot0 + bq;
+                        misc[4] = bq + 1; misc[5] = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            if (misc[4]) {
+                const int rq = misc[4] - 1;
+                uint32_t *dst = reinterpret_cast<uint32_t *>(a.best_cfg + (size_t)blk * np);
+                for (int c = tid; c < (np >> 2); c += NT) {
+                    uint32_t v = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool real = 4 * c + j < n;
+                        v |= (real ? (((Wsm[4 * c + j] >> rq) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
+                    }
+                    dst[c] = v;
+                }
+                __syncthreads();
+            }
+        }
+        // Store: bit words -> int8 spin rows (fields are not kept by this layout).
+        for (int c = tid; c < (np >> 2); c += NT) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w4[j] = Wsm[4 * c + j];
+            for (int r = 0; r < 32; ++r) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool real = 4 * c + j < n;
+                    v |= (real ? (((w4[j] >> r) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
+                }
+                *reinterpret_cast<uint32_t *>(a.spins_out + (size_t)(slot0 + r) * np + 4 * c) = v;
+            }
+        }
+        if (tid < 32) a.E_out[slot0 + tid] = Eacc[tid];
+        if (tid == 0 && misc[5]) a.best_rec[blk] = make_int4(misc[0], misc[1], misc[2], misc[3]);
+        const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, nacc);
+        if (act && lane == 0 && wsum) atomicAdd(&a.accepts[a.k], (unsigned long long)wsum);
+        __syncthreads();
+    }
+}
+
+template <bool W>
+void *msc_kernel(int mmax) {
+    if (mmax <= 7) return reinterpret_cast<void *>(&k_sweep_msc<3, W, 256, 4>);
+    if (mmax <= 15) return reinterpret_cast<void *>(&k_sweep_msc<4, W, 256, 4>);
+    if (mmax <= 31) return reinterpret_cast<void *>(&k_sweep_msc<5, W, 256, 4>);
+    if (mmax <= 63) return reinterpret_cast<void *>(&k_sweep_msc<6, W, 256, 4>);
+    return reinterpret_cast<void *>(&k_sweep_msc<7, W, 256, 4>);   // c <= 127: mb = 2c + 128 - deg stays in a byte
+}
+
 template <bool W>
 void *packed_kernel(int threads) {
     switch (threads) {
@@ -554,7 +726,8 @@ void *kernel_ptr() {
     return reinterpret_cast<void *>(&k_sweep<G, FB, W>);
 }
 
-void *select_kernel(int G, int fb, bool weighted, int threads) {
+void *select_kernel(int G, int fb, bool weighted, int threads, int mmax) {
+    if (fb == 1) return weighted ? msc_kernel<true>(mmax) : msc_kernel<false>(mmax);
     if (fb == 7) return weighted ? packed_kernel<true>(threads) : packed_kernel<false>(threads);
     if (G == 1) {
         if (fb == 16) return weighted ? kernel_ptr<1, 16, true>() : kernel_ptr<1, 16, false>();
@@ -569,7 +742,10 @@ void *select_kernel(int G, int fb, bool weighted, int threads) {
 cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int threads,
                             bool weighted, SweepConfig *cfg) {
     size_t smem;
-    if (field_bits == 7) {
+    if (field_bits == 1) {   // multi-spin coded: 32 replicas per word
+        G = 8;
+        smem = (size_t)g.np * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + (32 + 32 + 8) * 4;
+    } else if (field_bits == 7) {
         G = 1;
         smem = (size_t)(g.np + 32) * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + 16 * 4 +
                (size_t)((((g.np + 31) / 32) + 1) & ~1) * 4 + (size_t)(threads / 32) * PK_QCAP * 8;
@@ -580,13 +756,24 @@ cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int
         smem += (size_t)((g.ncol + 1 + 3) & ~3) * 4;
         smem += (size_t)(8 * G + 8) * 4;
     }
-    void *fn = select_kernel(G, field_bits, weighted, threads);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    void *fn = select_kernel(G, field_bits, weighted, threads, g.mmax);
+    // The attribute belongs to the kernel function, not to a context: only ever
+    // raise it, so that contexts configured earlier keep launching.
+    {
+        static std::mutex mu;
+        static std::unordered_map<void *, size_t> raised;
+        std::lock_guard<std::mutex> lock(mu);
+        size_t &cur = raised[fn];
+        if (smem > cur) {
+            cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            cur = smem;
+        }
+    }
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     const int nblk = (R + 4 * G - 1) / (4 * G);
@@ -599,7 +786,7 @@ cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int
 }
 
 cudaError_t launch_sweep(const SweepConfig &cfg, const SweepArgs &a, cudaStream_t st) {
-    void *fn = select_kernel(cfg.G, cfg.field_bits, a.g.wt != nullptr, cfg.threads);
+    void *fn = select_kernel(cfg.G, cfg.field_bits, a.g.wt != nullptr, cfg.threads, a.g.mmax);
     void *args[] = {const_cast<SweepArgs *>(&a)};
     return cudaLaunchKernel(fn, dim3(cfg.grid), dim3(cfg.threads), args, cfg.smem, st);
 }

@@ -224,6 +224,10 @@ int validate_opts(pa_ctx *c, const pa_anneal_opts &o) {
         return fail(c, PA_EINVAL, "8- and 7-bit fields need max degree <= 127");
     if (o.field_bits == 7 && !c->packed_ok)
         return fail(c, PA_EINVAL, "the packed layout needs n <= 32720");
+    if (o.variant == PA_VARIANT_MSC && c->maxdeg > 127)
+        return fail(c, PA_EINVAL, "the multi-spin-coded variant needs max degree <= 127");
+    if (o.variant == PA_VARIANT_MSC && o.threads_per_cta > 256)
+        return fail(c, PA_EINVAL, "the multi-spin-coded variant runs at most 256 threads per CTA");
     if (o.nlm_period < 0) return fail(c, PA_EINVAL, "nlm_period < 0");
     if (o.replicas_per_cta != 0 && o.replicas_per_cta != 4 && o.replicas_per_cta != 8)
         return fail(c, PA_EINVAL, "replicas_per_cta must be 0, 4 or 8");
@@ -468,13 +472,13 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     r.k_done = 0;
     r.launches = r.sweep_launches = 0;
     r.anneal_ms = r.sweep_ms = 0.0;
-    r.variant = PA_VARIANT_I8;
+    r.variant = o.variant == PA_VARIANT_MSC ? PA_VARIANT_MSC : PA_VARIANT_I8;
     // Sweep kernel shape.
+    const bool msc = o.variant == PA_VARIANT_MSC;
     int G = o.replicas_per_cta == 8 ? 2 : 1;
-    int threads = o.threads_per_cta ? o.threads_per_cta : (o.field_bits == 7 ? 128 : 512);
+    int threads = o.threads_per_cta ? o.threads_per_cta : (msc ? 256 : (o.field_bits == 7 ? 128 : 512));
     pa::GraphDev g = c->gdev();
-    cudaError_t ce = pa::sweep_configure(g, R, G, o.field_bits, threads, c->weighted, &r.sweep);
-    if (ce != cudaSuccess && o.replicas_per_cta == 0 && G == 1) return cuda_fail(c, ce, "sweep_configure");
+    cudaError_t ce = pa::sweep_configure(g, R, G, msc ? 1 : o.field_bits, threads, c->weighted, &r.sweep);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "sweep_configure");
     G = r.sweep.G;
     r.Rpad = ((R + 4 * G - 1) / (4 * G)) * 4 * G;
@@ -578,6 +582,124 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     return PA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// Enqueue temperature step k of the context's anneal on stream st.
+int enqueue_step(pa_ctx *c, int32_t k, cudaStream_t st, bool time_sweep) {
+    RunState &r = c->run;
+    pa::GraphDev g = c->gdev();
+    const uint32_t k0 = (uint32_t)r.seed, k1 = (uint32_t)(r.seed >> 32);
+    const pa_anneal_opts &o = r.opts;
+    const int cur = r.cur, nxt = 1 - r.cur;
+    pa::ResampleArgs ra{};
+    ra.E = r.E[cur].as<int32_t>();
+    ra.R = r.R;
+    ra.nch = r.nch;
+    ra.k = k;
+    ra.key0 = k0;
+    ra.key1 = k1;
+    ra.qpow = r.d_qpow.as<double>();
+    ra.qsel = o.adaptive ? r.ad_qsel.as<int32_t>() : nullptr;
+    ra.active = nullptr;   // the minimum runs before the adaptive decision
+    ra.emin = r.rec_emin.as<int32_t>();
+    ra.partA = r.partA.as<double>();
+    ra.partT = r.partT.as<unsigned long long>();
+    ra.tval = r.tval.as<unsigned long long>();
+    ra.ploc = r.ploc.as<unsigned long long>();
+    ra.parent = r.parent.as<int32_t>();
+    ra.recA = r.rec_A.as<double>();
+    ra.recT = r.rec_T.as<unsigned long long>();
+    ra.reco = r.rec_o.as<uint32_t>();
+    ra.counts = o.record_counts ? r.rec_counts.as<int32_t>() : nullptr;
+    ra.stamp = r.rec_stamp.as<unsigned long long>();
+    PA_CUDA(c, pa::launch_rs_min(ra, st));
+    r.launches += 1;
+    if (o.adaptive) {
+        pa::AdaptArgs aa{};
+        aa.E = r.E[cur].as<int32_t>();
+        aa.emin = r.rec_emin.as<int32_t>();
+        aa.R = r.R;
+        aa.k = k;
+        aa.J = o.adapt_J;
+        aa.nmax = r.ad_nmax;
+        aa.nch = r.nch;
+        aa.rhoR = o.rho * (double)r.R;
+        aa.delta = r.ad_delta;
+        aa.qpow = r.d_qpow.as<double>();
+        aa.part = r.ad_part.as<double>();
+        aa.state = r.ad_state.as<int32_t>();
+        aa.qsel = r.ad_qsel.as<int32_t>();
+        aa.active = r.ad_active.as<int32_t>();
+        aa.tidx = r.d_tidx.as<int32_t>();
+        aa.jsel = r.rec_jsel.as<int32_t>();
+        aa.beta = r.ad_beta.as<double>();
+        PA_CUDA(c, pa::launch_adapt(aa, st));
+        r.launches += 2;
+        ra.active = r.ad_active.as<int32_t>();
+    }
+    PA_CUDA(c, pa::launch_rs_rest(ra, st));
+    r.launches += 2;
+
+    pa::SweepArgs sa{};
+    sa.g = g;
+    sa.spins_in = r.spins[cur].as<int8_t>();
+    sa.fields_in = r.fields[cur].as<int16_t>();
+    sa.E_in = r.E[cur].as<int32_t>();
+    sa.spins_out = r.spins[nxt].as<int8_t>();
+    sa.fields_out = r.fields[nxt].as<int16_t>();
+    sa.E_out = r.E[nxt].as<int32_t>();
+    sa.parent = r.parent.as<int32_t>();
+    sa.tables = r.d_tables.as<uint32_t>();
+    sa.tidx = r.d_tidx.as<int32_t>();
+    sa.active = o.adaptive ? r.ad_active.as<int32_t>() : nullptr;
+    sa.R = r.R;
+    sa.nblk = r.nblk;
+    sa.S = r.S;
+    sa.k = k;
+    sa.key0 = k0;
+    sa.key1 = k1;
+    sa.best_rec = r.best_rec.as<int4>();
+    sa.best_cfg = r.best_cfg.as<int8_t>();
+    sa.accepts = r.rec_acc.as<unsigned long long>();
+    sa.sweep_emin = r.rec_sweep.as<int32_t>();
+    cudaEvent_t s0 = nullptr, s1 = nullptr;
+    if (o.time_kernels) {
+        PA_CUDA(c, cudaEventCreate(&s0));
+        PA_CUDA(c, cudaEventCreate(&s1));
+        r.ev_sweep.push_back(s0);
+        r.ev_sweep.push_back(s1);
+        PA_CUDA(c, cudaEventRecord(s0, st));
+    }
+    PA_CUDA(c, pa::launch_sweep(r.sweep, sa, st));
+    if (o.time_kernels) PA_CUDA(c, cudaEventRecord(s1, st));
+    r.launches += 1;
+    r.sweep_launches += 1;
+    r.cur = nxt;
+    if (o.nlm_period > 0 && k > 0 && k % o.nlm_period == 0) {
+        pa::NlmArgs na{};
+        na.g = g;
+        na.pos = c->d_pos.as<int32_t>();
+        na.spins = r.spins[nxt].as<int8_t>();
+        na.fields = r.fields[nxt].as<int16_t>();
+        na.E = r.E[nxt].as<int32_t>();
+        na.R = r.R;
+        na.k = k;
+        na.key0 = k0;
+        na.key1 = k1;
+        na.active = o.adaptive ? r.ad_active.as<int32_t>() : nullptr;
+        na.pairs = r.rec_nlm_pairs.as<int32_t>();
+        na.flips = r.rec_nlm_flips.as<unsigned long long>();
+        int nl = 0;
+        PA_CUDA(c, pa::launch_nonlocal(na, r.nlm_scratch.p, st, &nl));
+        r.launches += nl;
+    }
+    return PA_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int pa_anneal_run(pa_ctx *c, int32_t k_end) {
     if (!c) return PA_EINVAL;
     RunState &r = c->run;
@@ -585,120 +707,14 @@ int pa_anneal_run(pa_ctx *c, int32_t k_end) {
     if (k_end > r.K) k_end = r.K;
     if (k_end <= r.k_done) return PA_OK;
     cudaStream_t st = c->stream();
-    pa::GraphDev g = c->gdev();
-    const uint32_t k0 = (uint32_t)r.seed, k1 = (uint32_t)(r.seed >> 32);
     cudaEvent_t e0, e1;
     PA_CUDA(c, cudaEventCreate(&e0));
     PA_CUDA(c, cudaEventCreate(&e1));
     r.ev_pending.push_back(e0);
     r.ev_pending.push_back(e1);
     PA_CUDA(c, cudaEventRecord(e0, st));
-    const pa_anneal_opts &o = r.opts;
-    for (int32_t k = r.k_done; k < k_end; ++k) {
-        const int cur = r.cur, nxt = 1 - r.cur;
-        pa::ResampleArgs ra{};
-        ra.E = r.E[cur].as<int32_t>();
-        ra.R = r.R;
-        ra.nch = r.nch;
-        ra.k = k;
-        ra.key0 = k0;
-        ra.key1 = k1;
-        ra.qpow = r.d_qpow.as<double>();
-        ra.qsel = o.adaptive ? r.ad_qsel.as<int32_t>() : nullptr;
-        ra.active = nullptr;   // the minimum runs before the adaptive decision
-        ra.emin = r.rec_emin.as<int32_t>();
-        ra.partA = r.partA.as<double>();
-        ra.partT = r.partT.as<unsigned long long>();
-        ra.tval = r.tval.as<unsigned long long>();
-        ra.ploc = r.ploc.as<unsigned long long>();
-        ra.parent = r.parent.as<int32_t>();
-        ra.recA = r.rec_A.as<double>();
-        ra.recT = r.rec_T.as<unsigned long long>();
-        ra.reco = r.rec_o.as<uint32_t>();
-        ra.counts = o.record_counts ? r.rec_counts.as<int32_t>() : nullptr;
-        ra.stamp = r.rec_stamp.as<unsigned long long>();
-        PA_CUDA(c, pa::launch_rs_min(ra, st));
-        r.launches += 1;
-        if (o.adaptive) {
-            pa::AdaptArgs aa{};
-            aa.E = r.E[cur].as<int32_t>();
-            aa.emin = r.rec_emin.as<int32_t>();
-            aa.R = r.R;
-            aa.k = k;
-            aa.J = o.adapt_J;
-            aa.nmax = r.ad_nmax;
-            aa.nch = r.nch;
-            aa.rhoR = o.rho * (double)r.R;
-            aa.delta = r.ad_delta;
-            aa.qpow = r.d_qpow.as<double>();
-            aa.part = r.ad_part.as<double>();
-            aa.state = r.ad_state.as<int32_t>();
-            aa.qsel = r.ad_qsel.as<int32_t>();
-            aa.active = r.ad_active.as<int32_t>();
-            aa.tidx = r.d_tidx.as<int32_t>();
-            aa.jsel = r.rec_jsel.as<int32_t>();
-            aa.beta = r.ad_beta.as<double>();
-            PA_CUDA(c, pa::launch_adapt(aa, st));
-            r.launches += 2;
-            ra.active = r.ad_active.as<int32_t>();
-        }
-        PA_CUDA(c, pa::launch_rs_rest(ra, st));
-        r.launches += 2;
-
-        pa::SweepArgs sa{};
-        sa.g = g;
-        sa.spins_in = r.spins[cur].as<int8_t>();
-        sa.fields_in = r.fields[cur].as<int16_t>();
-        sa.E_in = r.E[cur].as<int32_t>();
-        sa.spins_out = r.spins[nxt].as<int8_t>();
-        sa.fields_out = r.fields[nxt].as<int16_t>();
-        sa.E_out = r.E[nxt].as<int32_t>();
-        sa.parent = r.parent.as<int32_t>();
-        sa.tables = r.d_tables.as<uint32_t>();
-        sa.tidx = r.d_tidx.as<int32_t>();
-        sa.active = o.adaptive ? r.ad_active.as<int32_t>() : nullptr;
-        sa.R = r.R;
-        sa.nblk = r.nblk;
-        sa.S = r.S;
-        sa.k = k;
-        sa.key0 = k0;
-        sa.key1 = k1;
-        sa.best_rec = r.best_rec.as<int4>();
-        sa.best_cfg = r.best_cfg.as<int8_t>();
-        sa.accepts = r.rec_acc.as<unsigned long long>();
-        sa.sweep_emin = r.rec_sweep.as<int32_t>();
-        cudaEvent_t s0 = nullptr, s1 = nullptr;
-        if (o.time_kernels) {
-            PA_CUDA(c, cudaEventCreate(&s0));
-            PA_CUDA(c, cudaEventCreate(&s1));
-            r.ev_sweep.push_back(s0);
-            r.ev_sweep.push_back(s1);
-            PA_CUDA(c, cudaEventRecord(s0, st));
-        }
-        PA_CUDA(c, pa::launch_sweep(r.sweep, sa, st));
-        if (o.time_kernels) PA_CUDA(c, cudaEventRecord(s1, st));
-        r.launches += 1;
-        r.sweep_launches += 1;
-        r.cur = nxt;
-        if (o.nlm_period > 0 && k > 0 && k % o.nlm_period == 0) {
-            pa::NlmArgs na{};
-            na.g = g;
-            na.pos = c->d_pos.as<int32_t>();
-            na.spins = r.spins[nxt].as<int8_t>();
-            na.fields = r.fields[nxt].as<int16_t>();
-            na.E = r.E[nxt].as<int32_t>();
-            na.R = r.R;
-            na.k = k;
-            na.key0 = k0;
-            na.key1 = k1;
-            na.active = o.adaptive ? r.ad_active.as<int32_t>() : nullptr;
-            na.pairs = r.rec_nlm_pairs.as<int32_t>();
-            na.flips = r.rec_nlm_flips.as<unsigned long long>();
-            int nl = 0;
-            PA_CUDA(c, pa::launch_nonlocal(na, r.nlm_scratch.p, st, &nl));
-            r.launches += nl;
-        }
-    }
+    for (int32_t k = r.k_done; k < k_end; ++k)
+        if (int rc = enqueue_step(c, k, st, r.opts.time_kernels != 0)) return rc;
     PA_CUDA(c, pa::launch_stamp(r.rec_stamp.as<unsigned long long>() + k_end, st));
     r.launches += 1;
     PA_CUDA(c, cudaEventRecord(e1, st));
@@ -748,6 +764,108 @@ int best_block(pa_ctx *c, int4 *rec) {
 }  // namespace
 
 extern "C" {
+
+int pa_batch_anneal(const pa_job *jobs, int32_t n_jobs, const pa_batch_opts *bopts, double *elapsed_ms) {
+    if (!jobs || n_jobs < 1) return PA_EINVAL;
+    pa_batch_opts bo{};
+    if (bopts) bo = *bopts;
+    int ns = bo.n_streams > 0 ? bo.n_streams : std::min<int>(n_jobs, 16);
+    if (ns > 64) ns = 64;
+    cudaStream_t origin = reinterpret_cast<cudaStream_t>(bo.stream);
+    cudaStream_t own_origin = nullptr;   // the legacy default stream cannot be captured
+    if (!origin && bo.use_graph) {
+        if (cudaStreamCreateWithFlags(&own_origin, cudaStreamNonBlocking) != cudaSuccess) return PA_ECUDA;
+        origin = own_origin;
+    }
+    std::vector<cudaStream_t> streams(ns, nullptr);
+    std::vector<cudaEvent_t> joins(ns, nullptr);
+    cudaEvent_t fork = nullptr, t0 = nullptr, t1 = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int rc = PA_OK;
+    auto cleanup = [&]() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        for (auto e : joins) if (e) cudaEventDestroy(e);
+        if (fork) cudaEventDestroy(fork);
+        if (t0) cudaEventDestroy(t0);
+        if (t1) cudaEventDestroy(t1);
+        for (int j = 0; j < n_jobs; ++j)
+            if (jobs[j].ctx) jobs[j].ctx->run.opts.stream = bo.stream;
+        for (auto st : streams) if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+        if (own_origin) { cudaStreamSynchronize(own_origin); cudaStreamDestroy(own_origin); }
+        cudaGetLastError();
+    };
+    auto cuda_err = [&](cudaError_t e, const char *where) {
+        fail(jobs[0].ctx, PA_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+        return PA_ECUDA;
+    };
+    for (int i = 0; i < ns; ++i) {
+        if (cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return PA_ECUDA;
+        }
+    }
+    if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) {
+        cleanup();
+        return PA_ECUDA;
+    }
+    int32_t kmax = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        if (!jobs[j].ctx) { cleanup(); return PA_EINVAL; }
+        pa_anneal_opts o = jobs[j].opts;
+        o.stream = streams[j % ns];
+        o.time_kernels = 0;
+        rc = pa_anneal_begin(jobs[j].ctx, jobs[j].betas, jobs[j].K, jobs[j].R, jobs[j].sweeps, jobs[j].seed, &o);
+        if (rc) { cleanup(); return rc; }
+        kmax = std::max(kmax, jobs[j].K);
+    }
+    for (auto st : streams) cudaStreamSynchronize(st);
+    if (cudaStreamSynchronize(origin) != cudaSuccess) { cleanup(); return PA_ECUDA; }
+    const bool use_graph = bo.use_graph != 0;
+    if (!use_graph) cudaEventRecord(t0, origin);
+    if (use_graph) {
+        cudaError_t e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            rc = cuda_err(e, "cudaStreamBeginCapture");
+            cleanup();
+            return rc;
+        }
+    }
+    cudaEventRecord(fork, origin);
+    for (auto st : streams) cudaStreamWaitEvent(st, fork, 0);
+    for (int32_t k = 0; k < kmax && rc == PA_OK; ++k)
+        for (int j = 0; j < n_jobs && rc == PA_OK; ++j)
+            if (k < jobs[j].K) rc = enqueue_step(jobs[j].ctx, k, streams[j % ns], false);
+    for (int j = 0; j < n_jobs && rc == PA_OK; ++j) {
+        RunState &r = jobs[j].ctx->run;
+        if (pa::launch_stamp(r.rec_stamp.as<unsigned long long>() + r.K, streams[j % ns]) != cudaSuccess) rc = PA_ECUDA;
+        r.launches += 1;
+        r.k_done = r.K;
+    }
+    for (int i = 0; i < ns; ++i) {
+        cudaEventRecord(joins[i], streams[i]);
+        cudaStreamWaitEvent(origin, joins[i], 0);
+    }
+    if (use_graph) {
+        cudaError_t e = cudaStreamEndCapture(origin, &graph);
+        if (rc == PA_OK && e != cudaSuccess) rc = cuda_err(e, "cudaStreamEndCapture");
+        if (rc == PA_OK && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+            rc = cuda_err(e, "cudaGraphInstantiate");
+        if (rc == PA_OK) {
+            cudaEventRecord(t0, origin);
+            if ((e = cudaGraphLaunch(exec, origin)) != cudaSuccess) rc = cuda_err(e, "cudaGraphLaunch");
+        }
+    }
+    cudaEventRecord(t1, origin);
+    if (cudaStreamSynchronize(origin) != cudaSuccess && rc == PA_OK) rc = PA_ECUDA;
+    float ms = 0.f;
+    if (rc == PA_OK && elapsed_ms && cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess) *elapsed_ms = ms;
+    cleanup();
+    return rc;
+}
 
 int pa_best_record(pa_ctx *c, int32_t *energy, int32_t *step, int32_t *sweep, int32_t *slot) {
     if (!c) return PA_EINVAL;

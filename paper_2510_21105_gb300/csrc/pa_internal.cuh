@@ -115,7 +115,7 @@ cudaError_t launch_stamp(unsigned long long *stamp, cudaStream_t st);
 
 struct SweepConfig {
     int G;          // replica groups of 4 per CTA (1 or 2)
-    int field_bits; // 16, 8, or 7 (packed spin + field byte)
+    int field_bits; // 16, 8, 7 (packed spin + field byte), or 1 (multi-spin coded)
     int threads;
     int grid;
     size_t smem;

@@ -61,12 +61,13 @@ def test_replay_g63like_nonlocal_step():
     _replay_check(g, betas, c["R"], c["S"], c["seed"], k, subset, nlm_period=k)
 
 
-def test_replay_torus100_full_population():
+@pytest.mark.parametrize("variant", [0, 1])
+def test_replay_torus100_full_population(variant):
     c = wl.CONFIGS["torus100"]
     g = c["graph"]()
     betas = wl.linear_betas(*c["beta"], c["K"])
     subset = np.array([0, 5, 31, 32767, 20000])
-    _replay_check(g, betas, c["R"], c["S"], c["seed"], 4, subset)
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], 4, subset, variant=variant)
 
 
 def test_full_g63like_anneal_properties():

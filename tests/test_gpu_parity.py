@@ -31,13 +31,13 @@ def test_tables_and_colouring_match_oracle():
     a.close()
 
 
-@pytest.mark.parametrize("field_bits", [0, 16])
-def test_parity_gnp800_full_workload(field_bits):
+@pytest.mark.parametrize("field_bits,variant", [(0, 0), (16, 0), (0, 1)])
+def test_parity_gnp800_full_workload(field_bits, variant):
     # N = 800, p = 0.06, R = 256, beta 0.1 -> 3.0 in 100 steps, 4 sweeps, seed 0.
     c = wl.CONFIGS["gnp800"]
     g = c["graph"]()
     betas = wl.linear_betas(*c["beta"], c["K"])
-    gpu = run_gpu(g, betas, c["R"], c["S"], c["seed"], field_bits=field_bits)
+    gpu = run_gpu(g, betas, c["R"], c["S"], c["seed"], field_bits=field_bits, variant=variant)
     orc = _oracle_cached("gnp800", lambda: run_oracle(g, betas, c["R"], c["S"], c["seed"]))
     assert_parity(gpu, orc, g, c["R"], c["S"])
 
@@ -54,7 +54,8 @@ def _oracle_cached(key, fn):
 @pytest.mark.parametrize("R,opts", [(6, {}), (6, {"field_bits": 16}), (13, {"field_bits": 8}),
                                     (1, {}), (1, {"field_bits": 16}), (7, {"field_bits": 7, "threads_per_cta": 256}),
                                     (24, {"replicas_per_cta": 8, "field_bits": 16}),
-                                    (40, {"replicas_per_cta": 8, "field_bits": 8, "threads_per_cta": 128})])
+                                    (40, {"replicas_per_cta": 8, "field_bits": 8, "threads_per_cta": 128}),
+                                    (6, {"variant": 1}), (33, {"variant": 1}), (70, {"variant": 1, "threads_per_cta": 128})])
 def test_parity_ragged_signed(R, opts):
     g = wl.from_edges(37, *_random_edges(37, 90, seed=R), name="ragged")
     betas = wl.linear_betas(0.05, 2.5, 7)
@@ -75,19 +76,21 @@ def _random_edges(n, m, seed):
     return e[:, 0], e[:, 1], w
 
 
-def test_parity_torus_two_colour_checkerboard():
+@pytest.mark.parametrize("variant", [0, 1])
+def test_parity_torus_two_colour_checkerboard(variant):
     g = wl.torus(24, seed=5)
     betas = wl.linear_betas(0.1, 3.5, 12)
-    gpu = run_gpu(g, betas, 64, 4, seed=9)
+    gpu = run_gpu(g, betas, 64, 4, seed=9, variant=variant)
     orc = run_oracle(g, betas, 64, 4, seed=9)
     assert gpu["stats"]["n_colours"] == 2
     assert_parity(gpu, orc, g, 64, 4)
 
 
-def test_parity_nonlocal_moves():
+@pytest.mark.parametrize("variant", [0, 1])
+def test_parity_nonlocal_moves(variant):
     g = wl.gnm(500, 3000, seed=7)
     betas = wl.linear_betas(0.1, 3.0, 13)
-    gpu = run_gpu(g, betas, 64, 3, seed=11, nlm_period=3)
+    gpu = run_gpu(g, betas, 64, 3, seed=11, nlm_period=3, variant=variant)
     orc = run_oracle(g, betas, 64, 3, seed=11, nlm_period=3)
     assert orc.step_nlm_pairs.sum() > 0
     assert_parity(gpu, orc, g, 64, 3)
@@ -160,5 +163,6 @@ def test_repeat_runs_are_identical_and_launch_shape_free():
     r3 = run_gpu(g, betas, 64, 3, seed=77, replicas_per_cta=8, threads_per_cta=1024, field_bits=16)
     r4 = run_gpu(g, betas, 64, 3, seed=77, field_bits=8)
     r5 = run_gpu(g, betas, 64, 3, seed=77, field_bits=16)
-    for r in (r2, r3, r4, r5):
+    r6 = run_gpu(g, betas, 64, 3, seed=77, variant=1)
+    for r in (r2, r3, r4, r5, r6):
         assert np.array_equal(r1["spins"], r["spins"]) and r1["best"] == r["best"]
