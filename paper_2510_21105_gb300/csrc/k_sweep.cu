@@ -554,6 +554,51 @@ __device__ __forceinline__ uint32_t spread_nibble(uint32_t nib) {   // bit q -> 
     return (nib * 0x00204081u) & 0x01010101u;
 }
 
+// Philox4x32-10 for the eight counters (c0, c1_g, c2, c3) of one item, which
+// differ only in word 1: the products of rounds 1-3 whose inputs do not depend
+// on c1 are computed once (the result is identical to philox10 of each counter).
+struct PhiloxShared {
+    uint32_t u1;      // round 1: hi(M1 c2) ^ k0        (uniform)
+    uint32_t l1;      // round 1: lo(M1 c2)              (uniform)
+    uint32_t a, b;    // round 1: hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)
+    uint32_t s0, s1;  // round 2: hi(M1 a) ^ l1 ^ k0', lo(M1 a)
+    uint32_t h3, l3;  // round 3: hi(M0 s0), lo(M0 s0)
+};
+
+__device__ __forceinline__ PhiloxShared philox_shared(uint32_t c0, uint32_t c2, uint32_t c3, uint32_t k0,
+                                                      uint32_t k1) {
+    PhiloxShared p;
+    p.u1 = __umulhi(0xCD9E8D57u, c2) ^ k0;
+    p.l1 = 0xCD9E8D57u * c2;
+    p.a = __umulhi(0xD2511F53u, c0) ^ c3 ^ k1;
+    p.b = 0xD2511F53u * c0;
+    p.s0 = __umulhi(0xCD9E8D57u, p.a) ^ p.l1 ^ (k0 + 0x9E3779B9u);
+    p.s1 = 0xCD9E8D57u * p.a;
+    p.h3 = __umulhi(0xD2511F53u, p.s0);
+    p.l3 = 0xD2511F53u * p.s0;
+    return p;
+}
+
+__device__ __forceinline__ uint4 philox_from_shared(const PhiloxShared &p, uint32_t c1, uint32_t k0, uint32_t k1) {
+    // round 1 (only word 0 depends on c1)
+    const uint32_t n0 = p.u1 ^ c1;
+    // round 2: word 2 product shared (s0, s1); word 0 product per counter
+    uint4 c = make_uint4(p.s0, p.s1, __umulhi(0xD2511F53u, n0) ^ p.b ^ (k1 + 0xBB67AE85u), 0xD2511F53u * n0);
+    // round 3: word 0 product shared (h3, l3)
+    k0 += 2u * 0x9E3779B9u;
+    k1 += 2u * 0xBB67AE85u;
+    c = make_uint4(__umulhi(0xCD9E8D57u, c.z) ^ c.y ^ k0, 0xCD9E8D57u * c.z, p.h3 ^ c.w ^ k1, p.l3);
+#pragma unroll
+    for (int r = 3; r < 10; ++r) {
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), hi1 = __umulhi(0xCD9E8D57u, c.z);
+        const uint32_t lo0 = 0xD2511F53u * c.x, lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
 template <int NPL, bool WEIGHTED, int NTB, int MINB>
 __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -623,6 +668,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
                         }
                     }
                     const uint32_t base = 128u - (e1 - e0);   // mb = 2c + 128 - deg
+                    const PhiloxShared ps = philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1);
                     uint32_t acc32 = 0;
 #pragma unroll 2
                     for (int g = 0; g < 8; ++g) {
@@ -630,8 +676,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
 #pragma unroll
                         for (int b = 0; b < NPL; ++b) cb |= spread_nibble((pl[b] >> (4 * g)) & 0xFu) << b;
                         const uint32_t mb = (cb << 1) + base * 0x01010101u;
-                        const uint4 u = philox10(make_uint4(vid, (uint32_t)(blk * 8 + g), (uint32_t)a.k, c3),
-                                                 a.key0, a.key1);
+                        const uint4 u = philox_from_shared(ps, (uint32_t)(blk * 8 + g), a.key0, a.key1);
                         const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {

@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -25,23 +26,41 @@ pa_alloc_fn g_alloc = nullptr;
 pa_free_fn g_free = nullptr;
 void *g_alloc_user = nullptr;
 
-void *dev_alloc(size_t bytes) {
+// Default device allocator: stream-ordered (cudaMallocAsync / cudaFreeAsync on
+// the owning context's stream), so releasing a finished context never
+// synchronises the device; the default pool keeps freed memory for reuse.
+void *dev_alloc(size_t bytes, cudaStream_t st) {
     if (bytes == 0) bytes = 16;
     if (g_alloc) return g_alloc(bytes, g_alloc_user);
+    static std::once_flag pool_once;
+    std::call_once(pool_once, []() {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
     void *p = nullptr;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
     return p;
 }
 
+// Frees are enqueued on the legacy default stream. Every caller has already
+// synchronised the owning context's stream (pa_destroy, and pa_anneal_begin
+// before it regrows a buffer), so no work still uses the memory; no stream
+// handle is kept, since the stream an allocation was made on (for example a
+// batch's temporary stream) may no longer exist when the buffer is freed.
 void dev_free(void *p) {
     if (!p) return;
     if (g_free)
         g_free(p, g_alloc_user);
     else
-        cudaFree(p);
+        cudaFreeAsync(p, nullptr);
 }
 
 struct DevBuf {
@@ -56,10 +75,10 @@ struct DevBuf {
         p = nullptr;
         bytes = 0;
     }
-    bool alloc(size_t b) {
+    bool alloc(size_t b, cudaStream_t stream = nullptr) {
         if (p && bytes >= b) return true;
         release();
-        p = dev_alloc(b);
+        p = dev_alloc(b, stream);
         if (!p) return false;
         bytes = b;
         return true;
@@ -274,7 +293,7 @@ void pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_fn, void *user) {
 void pa_default_opts(pa_anneal_opts *o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
-    o->variant = PA_VARIANT_I8;
+    o->variant = PA_VARIANT_AUTO;
     o->field_bits = 0;
     o->rho = 0.5;
     o->adapt_J = 8;
@@ -436,7 +455,7 @@ void pa_destroy(pa_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream());
     free_run_events(ctx->run);
     cudaGetLastError();
-    delete ctx;
+    delete ctx;   // buffers return to the pool on their own streams
 }
 
 int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_t sweeps,
@@ -445,6 +464,16 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     pa_anneal_opts o;
     pa_default_opts(&o);
     if (opts) o = *opts;
+    if (o.variant == PA_VARIANT_AUTO) {
+        // Multi-spin coding is fastest once its 32-replica blocks fill the GPU
+        // (two per SM); otherwise the 4-replica layouts give more blocks.
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const bool msc_fills = (R + 31) / 32 >= 2 * (sms > 0 ? sms : 152);
+        o.variant = (c->maxdeg <= 127 && msc_fills && o.field_bits == 0 &&
+                     (o.threads_per_cta == 0 || o.threads_per_cta <= 256)) ? PA_VARIANT_MSC : PA_VARIANT_I8;
+    }
     if (o.field_bits == 0) o.field_bits = (c->maxdeg <= 127 && c->packed_ok) ? 7 : 16;
     if (K < 0 || R < 1 || R > 65536 || sweeps < 0 || sweeps >= (1 << 28))
         return fail(c, PA_EINVAL, "K, R (1..65536) or sweeps out of range");
@@ -513,29 +542,30 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
         for (int32_t dn = 1; dn <= r.nq; ++dn)
             qpow_row(std::exp(-((double)dn * r.ad_delta)), &r.qpow[(size_t)(dn - 1) * 32]);
     }
-    // Device buffers.
+    // Device buffers (stream-ordered on the context's stream).
+    cudaStream_t ST = c->stream();
     const size_t npR = (size_t)c->np * r.Rpad;
     const int32_t Kc = std::max(K, 1);
     const int32_t Sc = std::max(sweeps, 1);
     const size_t nrs = (size_t)r.nch * pa::RS_CHUNK;
-    bool ok = r.spins[0].alloc(npR) && r.spins[1].alloc(npR) && r.fields[0].alloc(2 * npR) &&
-              r.fields[1].alloc(2 * npR) && r.E[0].alloc(4 * (size_t)r.Rpad) &&
-              r.E[1].alloc(4 * (size_t)r.Rpad) && r.parent.alloc(4 * (size_t)r.Rpad) &&
-              r.partA.alloc(8 * (size_t)r.nch) && r.partT.alloc(8 * (size_t)r.nch) &&
-              r.tval.alloc(8 * nrs) && r.ploc.alloc(8 * nrs) &&
-              r.d_tables.alloc(4 * r.tables.size()) && r.d_tidx.alloc(4 * (size_t)Kc) &&
-              r.d_qpow.alloc(8 * r.qpow.size()) && r.rec_emin.alloc(4 * (size_t)Kc) &&
-              r.rec_A.alloc(8 * (size_t)Kc) && r.rec_T.alloc(8 * (size_t)Kc) &&
-              r.rec_o.alloc(4 * (size_t)Kc) && r.rec_acc.alloc(8 * (size_t)Kc) &&
-              r.rec_sweep.alloc(4 * (size_t)Kc * Sc) && r.rec_stamp.alloc(8 * (size_t)(Kc + 1)) &&
-              r.rec_nlm_pairs.alloc(4 * (size_t)Kc) && r.rec_nlm_flips.alloc(8 * (size_t)Kc) &&
-              r.rec_jsel.alloc(4 * (size_t)Kc) && r.best_rec.alloc(16 * (size_t)r.nblk) &&
-              r.best_cfg.alloc((size_t)r.nblk * c->np);
-    if (ok && o.record_counts) ok = r.rec_counts.alloc(4 * (size_t)Kc * R);
+    bool ok = r.spins[0].alloc(npR, ST) && r.spins[1].alloc(npR, ST) && r.fields[0].alloc(2 * npR, ST) &&
+              r.fields[1].alloc(2 * npR, ST) && r.E[0].alloc(4 * (size_t)r.Rpad, ST) &&
+              r.E[1].alloc(4 * (size_t)r.Rpad, ST) && r.parent.alloc(4 * (size_t)r.Rpad, ST) &&
+              r.partA.alloc(8 * (size_t)r.nch, ST) && r.partT.alloc(8 * (size_t)r.nch, ST) &&
+              r.tval.alloc(8 * nrs, ST) && r.ploc.alloc(8 * nrs, ST) &&
+              r.d_tables.alloc(4 * r.tables.size(), ST) && r.d_tidx.alloc(4 * (size_t)Kc, ST) &&
+              r.d_qpow.alloc(8 * r.qpow.size(), ST) && r.rec_emin.alloc(4 * (size_t)Kc, ST) &&
+              r.rec_A.alloc(8 * (size_t)Kc, ST) && r.rec_T.alloc(8 * (size_t)Kc, ST) &&
+              r.rec_o.alloc(4 * (size_t)Kc, ST) && r.rec_acc.alloc(8 * (size_t)Kc, ST) &&
+              r.rec_sweep.alloc(4 * (size_t)Kc * Sc, ST) && r.rec_stamp.alloc(8 * (size_t)(Kc + 1), ST) &&
+              r.rec_nlm_pairs.alloc(4 * (size_t)Kc, ST) && r.rec_nlm_flips.alloc(8 * (size_t)Kc, ST) &&
+              r.rec_jsel.alloc(4 * (size_t)Kc, ST) && r.best_rec.alloc(16 * (size_t)r.nblk, ST) &&
+              r.best_cfg.alloc((size_t)r.nblk * c->np, ST);
+    if (ok && o.record_counts) ok = r.rec_counts.alloc(4 * (size_t)Kc * R, ST);
     if (ok && o.adaptive)
-        ok = r.ad_state.alloc(16) && r.ad_qsel.alloc(4 * (size_t)Kc) && r.ad_active.alloc(4 * (size_t)Kc) &&
-             r.ad_beta.alloc(8 * (size_t)Kc) && r.ad_part.alloc(16 * (size_t)(o.adapt_J + 1) * r.nch);
-    if (ok && o.nlm_period > 0) ok = r.nlm_scratch.alloc(pa::nlm_scratch_bytes(R));
+        ok = r.ad_state.alloc(16, ST) && r.ad_qsel.alloc(4 * (size_t)Kc, ST) && r.ad_active.alloc(4 * (size_t)Kc, ST) &&
+             r.ad_beta.alloc(8 * (size_t)Kc, ST) && r.ad_part.alloc(16 * (size_t)(o.adapt_J + 1) * r.nch, ST);
+    if (ok && o.nlm_period > 0) ok = r.nlm_scratch.alloc(pa::nlm_scratch_bytes(R), ST);
     if (!ok) return fail(c, PA_ENOMEM, "device allocation failed");
     cudaStream_t st = c->stream();
     PA_CUDA(c, copy(c, r.d_tables.p, r.tables.data(), 4 * r.tables.size(), cudaMemcpyHostToDevice, st, true));

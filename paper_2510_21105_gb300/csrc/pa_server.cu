@@ -1,11 +1,11 @@
 // pa_server.cu -- continuous-batching request loop over the library's anneals.
 //
-// A background host thread owns every CUDA call of the server:
-//   admission   requests wait in FIFO order until their estimated device
+// Two background host threads make every CUDA call of the server:
+//   admission   (admission thread) requests wait in FIFO order until their estimated device
 //               memory fits under the HBM budget (the oldest request is
 //               always admitted when nothing else runs), then get a context
 //               (graph upload) and an initialised population;
-//   ticks       each active request (at most n_streams at once, each on its
+//   ticks       (tick thread) each active request (at most n_streams at once, each on its
 //               own stream) gets its next steps_per_tick temperature steps
 //               enqueued; a request keeps at most two ticks in flight, so
 //               arrivals join within one tick;
@@ -70,7 +70,8 @@ struct pa_server {
     std::map<uint64_t, std::shared_ptr<Request>> all;
     uint64_t next_id = 1;
     bool stopping = false;
-    std::thread worker;
+    int preparing = 0;                // requests being admitted by the admission thread
+    std::thread worker, admitter;
     Clock::time_point t0;
     pa_server_stats_t stats{};
 };
@@ -156,36 +157,55 @@ bool admit_one(pa_server *s, const std::shared_ptr<Request> &q) {
     return true;
 }
 
+// Admission thread: moves queued requests to the active set (graph upload,
+// tables, population initialisation) while the tick thread keeps the device
+// busy with the requests already running.
+void admission_loop(pa_server *s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        std::shared_ptr<Request> q;
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            for (;;) {
+                if (!s->queue.empty()) {
+                    auto &f = s->queue.front();
+                    const bool idle = s->active.empty() && s->preparing == 0;
+                    if (idle || (s->used + f->bytes <= s->budget &&
+                                 (int32_t)s->active.size() + s->preparing < s->slots))
+                        break;
+                } else if (s->stopping) {
+                    return;
+                }
+                s->cv.wait_for(lock, std::chrono::milliseconds(2));
+            }
+            q = s->queue.front();
+            s->queue.pop_front();
+            s->used += q->bytes;
+            s->preparing += 1;
+        }
+        admit_one(s, q);
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            s->preparing -= 1;
+        }
+        s->cv.notify_all();
+    }
+}
+
+// Tick thread: retires finished ticks and requests, enqueues new ticks.
 void worker_loop(pa_server *s) {
     cudaSetDevice(s->device);
     for (;;) {
-        // Admission.
-        for (;;) {
-            std::shared_ptr<Request> q;
-            {
-                std::lock_guard<std::mutex> lock(s->mu);
-                if (s->queue.empty()) break;
-                auto &f = s->queue.front();
-                if (!s->active.empty() &&
-                    (s->used + f->bytes > s->budget || (int32_t)s->active.size() >= s->slots))
-                    break;
-                q = f;
-                s->queue.pop_front();
-                s->used += q->bytes;
-            }
-            admit_one(s, q);
-        }
         std::vector<std::shared_ptr<Request>> act;
         {
             std::unique_lock<std::mutex> lock(s->mu);
-            if (s->active.empty() && s->queue.empty()) {
-                if (s->stopping) return;
-                s->cv.wait_for(lock, std::chrono::milliseconds(5));
+            if (s->active.empty()) {
+                if (s->stopping && s->queue.empty() && s->preparing == 0) return;
+                s->cv.wait_for(lock, std::chrono::milliseconds(2));
                 continue;
             }
             act = s->active;
         }
-        // Retire finished ticks and completed requests.
         bool progressed = false;
         for (auto &q : act) {
             while (!q->inflight.empty() && cudaEventQuery(q->inflight.front()) == cudaSuccess) {
@@ -205,7 +225,7 @@ void worker_loop(pa_server *s) {
                             s->active.end());
             act = s->active;
         }
-        // Enqueue the next tick of every request with fewer than two in flight.
+        if (progressed) s->cv.notify_all();
         for (auto &q : act) {
             if (q->k_enq >= q->K || q->inflight.size() >= 2) continue;
             const int32_t k_end = std::min(q->K, q->k_enq + s->steps_per_tick);
@@ -221,7 +241,7 @@ void worker_loop(pa_server *s) {
             }
             progressed = true;
         }
-        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(200));
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(100));
     }
 }
 
@@ -239,6 +259,7 @@ int pa_server_start(pa_server **out, size_t hbm_budget_bytes, int32_t n_streams,
     s->slots = n_streams ? n_streams : 16;
     s->t0 = Clock::now();
     s->worker = std::thread(worker_loop, s);
+    s->admitter = std::thread(admission_loop, s);
     *out = s;
     return PA_OK;
 }
@@ -318,6 +339,7 @@ int pa_server_stop(pa_server *s) {
         s->stopping = true;
     }
     s->cv.notify_all();
+    if (s->admitter.joinable()) s->admitter.join();
     if (s->worker.joinable()) s->worker.join();
     delete s;
     return PA_OK;

@@ -46,7 +46,7 @@ def test_host_only_calls(lib):
     assert B.lib().pa_version() >= 10000
     assert B.strerror(B.PA_EINVAL) == "invalid argument"
     o = B.pa_default_opts()
-    assert o.field_bits == 0 and o.nlm_period == 0 and o.adaptive == 0
+    assert o.field_bits == 0 and o.nlm_period == 0 and o.adaptive == 0 and o.variant == B.PA_VARIANT_AUTO
 
 
 def _bad(n, rp, col, w=None):
