@@ -348,12 +348,15 @@ def run_batch(args):
     inst = wl.batch_instances(args.instances, seed=0)
     cache = os.path.join(tempfile.gettempdir(), "pa_autotune_cache.json")
     t0 = time.perf_counter()
-    opts = []
+    opts, opts_b = [], []
+    cand = [c for c in autotune.CANDIDATES if c.get("variant") == 1 or c.get("field_bits") == 7]
     for i, it in enumerate(inst):
         g = it["graph"]
-        cand = [c for c in autotune.CANDIDATES if c.get("variant") == 1 or c.get("field_bits") == 7]
         o, _ = autotune.tune(g, betas, it["R"], S, seed=it["seed"], steps=1, cache_path=cache, candidates=cand)
+        ob, _ = autotune.tune(g, betas, it["R"], S, seed=it["seed"], steps=1, cache_path=cache,
+                              candidates=cand, context="saturated")
         opts.append(o)
+        opts_b.append(ob)
     tune_s = time.perf_counter() - t0
     attempts = sum(it["graph"].n * it["R"] * S * K for it in inst)
     anns = [B.Annealer.from_graph(it["graph"]) for it in inst]
@@ -370,7 +373,7 @@ def run_batch(args):
     ev1.record()
     torch.cuda.synchronize()
     plain_ms = ev0.elapsed_time(ev1)
-    items = [(ann, betas, it["R"], S, it["seed"], K, o) for ann, it, o in zip(anns, inst, opts)]
+    items = [(ann, betas, it["R"], S, it["seed"], K, o) for ann, it, o in zip(anns, inst, opts_b)]
     B.pa_batch_anneal(items, n_streams=16, use_graph=True)   # warm-up (and graph build)
     times = [B.pa_batch_anneal(items, n_streams=16, use_graph=True) for _ in range(max(args.steps, 1))]
     batch_ms = statistics.median(times)
@@ -382,7 +385,8 @@ def run_batch(args):
             "ratio": plain_ms / batch_ms, "batch_ms": batch_ms, "plain_ms": plain_ms,
             "bit_identical_to_plain": same, "instances": len(inst), "attempts": attempts,
             "autotune_s": tune_s,
-            "layouts": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts)),
+            "layouts_plain": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts)),
+            "layouts_batched": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts_b)),
             "config": {"workload": "N~U[800,20000] random(p=12/(N-1))/torus/Delaunay, R 1024/4096/16384, "
                                    "beta 0.1->3.0 K=200 S=4", "use_graph": True, "n_streams": 16}}
     print(json.dumps(line), flush=True)
@@ -412,7 +416,10 @@ def _serve_trace(seconds, rate, seed=1):
     return trace
 
 
-def _serve(trace, betas, slots):
+def _serve(trace, betas, slots, saturated):
+    """saturated: other requests keep the GPU full, so each request uses the
+    kernel with the cheapest attempt (multi-spin coded); otherwise each uses
+    the automatic choice for a GPU of its own."""
     from paper_2510_21105_gb300 import binding as B
 
     with B.Server(200 << 30, n_streams=slots, steps_per_tick=8) as srv:
@@ -422,7 +429,8 @@ def _serve(trace, betas, slots):
             delay = at - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            ids.append(srv.submit(g, betas, R, 4, seed))
+            variant = 1 if (saturated and g.maxdeg <= 127) else 2
+            ids.append(srv.submit(g, betas, R, 4, seed, variant=variant))
         res = {}
         while len(res) < len(ids):
             for rid in ids:
@@ -448,8 +456,8 @@ def run_serve(args):
     torch.cuda.set_device(0)
     betas = wl.linear_betas(0.1, 3.0, 200)
     trace = _serve_trace(args.serve_seconds, args.rate)
-    served = _serve(trace, betas, slots=16)
-    plain = _serve(trace, betas, slots=1)
+    served = _serve(trace, betas, slots=16, saturated=True)
+    plain = _serve(trace, betas, slots=1, saturated=False)
     line = {"mode": "serve", "metric": "served attempts/s with continuous batching vs plain one-at-a-time",
             "value": served["attempts_per_s"], "unit": UNIT, "plain_value": plain["attempts_per_s"],
             "ratio": served["attempts_per_s"] / plain["attempts_per_s"],

@@ -45,10 +45,17 @@ def shape_key(g, R, S) -> str:
     return f"n{g.n}_m{g.m}_d{g.maxdeg}_w{int(g.w is not None)}_R{R}_S{S}"
 
 
-def tune(g, betas, R, S, seed=0, steps=2, cache_path=None, candidates=None):
-    """Return (best option dict, {candidate index: ms per sweep launch})."""
+def tune(g, betas, R, S, seed=0, steps=2, cache_path=None, candidates=None, context="alone"):
+    """Return (best option dict, {candidate index: ms per million attempts}).
+
+    context "alone": the instance has the GPU to itself, so a candidate must
+    also fill the GPU with its blocks (R as given).
+    context "saturated": other work keeps the GPU full (batches, a loaded
+    server), so candidates are compared by the cost of an attempt with the
+    GPU filled (R raised to at least 16384 for the timing run)."""
     cache = {}
-    key = shape_key(g, R, S)
+    key = shape_key(g, R, S) + ("" if context == "alone" else "_" + context)
+    R_run = R if context == "alone" else max(R, 16384)
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
             cache = json.load(f)
@@ -61,11 +68,11 @@ def tune(g, betas, R, S, seed=0, steps=2, cache_path=None, candidates=None):
     with B.Annealer.from_graph(g) as a:
         for i, cand in enumerate(cands):
             try:
-                a.begin(sl, R, S, seed, time_kernels=1, **cand)
+                a.begin(sl, R_run, S, seed, time_kernels=1, **cand)
                 a.run(len(sl))
                 a.sync()
                 st = a.stats()
-                times[i] = st["sweep_ms"] / max(st["sweep_launches"], 1)
+                times[i] = st["sweep_ms"] / max(st["attempts"], 1) * 1e6
             except B.PaError:
                 continue
     best = min(times, key=times.get)

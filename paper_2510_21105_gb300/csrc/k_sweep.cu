@@ -672,10 +672,13 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
                     uint32_t acc32 = 0;
 #pragma unroll 2
                     for (int g = 0; g < 8; ++g) {
-                        uint32_t cb = 0;
+                        // Byte q of 2c: bit b of nibble g of plane b moved to bit 8q + b + 1
+                        // (the multiply spreads the four bits, the mask keeps them).
+                        uint32_t c2 = 0;
 #pragma unroll
-                        for (int b = 0; b < NPL; ++b) cb |= spread_nibble((pl[b] >> (4 * g)) & 0xFu) << b;
-                        const uint32_t mb = (cb << 1) + base * 0x01010101u;
+                        for (int b = 0; b < NPL; ++b)
+                            c2 |= (((pl[b] >> (4 * g)) & 0xFu) * (0x00204081u << (b + 1))) & (0x02020202u << b);
+                        const uint32_t mb = c2 + base * 0x01010101u;
                         const uint4 u = philox_from_shared(ps, (uint32_t)(blk * 8 + g), a.key0, a.key1);
                         const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
