@@ -195,6 +195,22 @@ def sweep_roofline(stats, attempts_per_launch, peaks, kernel):
             "smem_frac": attempts_per_launch * 6.6 / t / (SMS * 128 * clk * 1e6)}
 
 
+def max_over_ranks(x: float, dist, device: str = "cpu") -> float:
+    """The slowest rank's time (every rank anneals its own instance)."""
+    if not dist:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(attempts_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job attempts per second: all ranks' attempts over the slowest rank's time."""
+    return world * attempts_per_rank / (ms_max / 1e3)
+
+
 def run_ours(args, rank, world, dist):
     import torch
 
@@ -257,12 +273,8 @@ def run_ours(args, rank, world, dist):
     t_best = st["t_best_ms"]
     acc_rate = st["accepts"] / max(st["attempts"], 1)
     cut, _, best_step, _ = ann.best()
-    ms_max = ms
-    if dist:
-        tt = torch.tensor([ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_max = float(tt.item())
-    value = world * attempts / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = aggregate_value(attempts, world, ms_max)
     clocks = clk.summary()
     roof = sweep_roofline(stats_acc, g.n * R * S, peaks, kernel)
     ann.close()
@@ -296,11 +308,7 @@ def run_ours(args, rank, world, dist):
             if it > 0:   # the first call pays the context's one-time set-up
                 times.append(dt)
                 h2d, d2h = st2["h2d_bytes"], st2["d2h_bytes"]
-        e2e_s = max(statistics.median(times), 1e-9)
-        if dist:
-            tt = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = max_over_ranks(max(statistics.median(times), 1e-9), dist, "cuda")
         e2e = {"value": world * attempts / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
 
