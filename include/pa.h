@@ -116,6 +116,9 @@ typedef struct {
     int64_t *nlm_flips;       /* spins flipped per replica by those moves */
     int32_t *jsel;            /* adaptive: chosen level j (-1 otherwise) */
     int32_t *counts;          /* copy counts n_r (record_counts = 1) */
+    double *t_ms;             /* device time from the start of step 0 to the
+                                 end of step k (global timer; includes any
+                                 host gap between pa_anneal_run calls) */
 } pa_step_arrays;
 
 /* Fill *o with the defaults listed above. */
@@ -185,6 +188,16 @@ int pa_get_state(pa_ctx *ctx, int8_t *spins, int32_t *energies);
  * mark `steps_done` steps as completed (resume / replay). Fields and energies
  * are recomputed on the device. Errors: PA_ESTATE, PA_EINVAL. */
 int pa_set_state(pa_ctx *ctx, const int8_t *spins, int32_t steps_done);
+
+/* Energies E = sum over edges w_ij x_i x_j and cuts (W - E)/2 (Eq. 1 and
+ * the sign convention of Sec. 2) of R host configurations int8[R][n] (+1/-1,
+ * vertex order), evaluated on the device with the kernel that initialises a
+ * population. Independent of any anneal: a verifier for configurations read
+ * back from files (e.g. the hexadecimal format of Sec. 3). energies int32[R]
+ * and cuts int64[R] are caller buffers; either may be NULL. R = 0 is a no-op.
+ * Allocates R*(3n + 4) bytes of device memory for the call. Errors: PA_EINVAL
+ * (spin not +1/-1, R < 0), PA_ENOMEM, PA_ECUDA. */
+int pa_energies(pa_ctx *ctx, const int8_t *spins, int32_t R, int32_t *energies, int64_t *cuts);
 
 /* Checkpoint: write the anneal parameters, the population and the best
  * record to `path`; pa_load restores them into a context created for the

@@ -48,7 +48,7 @@ class pa_stats_t(C.Structure):
 class pa_step_arrays(C.Structure):
     _fields_ = [(name, C.c_void_p) for name in
                 ("beta", "emin", "A", "T", "o", "accepts", "lnZ", "sweep_emin", "nlm_pairs",
-                 "nlm_flips", "jsel", "counts")]
+                 "nlm_flips", "jsel", "counts", "t_ms")]
 
 
 class pa_job(C.Structure):
@@ -113,6 +113,7 @@ def lib():
                                    C.c_int),
                 "pa_get_state": ([vp, vp, vp], C.c_int),
                 "pa_set_state": ([vp, vp, i32], C.c_int),
+                "pa_energies": ([vp, vp, i32, vp, vp], C.c_int),
                 "pa_save": ([vp, C.c_char_p], C.c_int),
                 "pa_load": ([vp, C.c_char_p], C.c_int),
                 "pa_stats": ([vp, C.POINTER(pa_stats_t)], C.c_int),
@@ -144,7 +145,7 @@ def exported_symbols():
     """Names declared in include/pa.h that the loaded library must export."""
     return ["pa_version", "pa_strerror", "pa_last_error", "pa_default_opts", "pa_create",
             "pa_destroy", "pa_anneal", "pa_anneal_begin", "pa_anneal_run", "pa_sync", "pa_best",
-            "pa_best_record", "pa_get_state", "pa_set_state", "pa_save", "pa_load", "pa_stats",
+            "pa_best_record", "pa_get_state", "pa_set_state", "pa_energies", "pa_save", "pa_load", "pa_stats",
             "pa_step_stats", "pa_tables", "pa_colouring", "pa_set_allocator", "pa_run_info",
             "pa_resample_noalloc", "pa_batch_anneal", "pa_server_start", "pa_server_submit",
             "pa_server_poll", "pa_server_result", "pa_server_stats", "pa_server_stop"]
@@ -243,6 +244,20 @@ def pa_set_state(ctx, spins, steps_done: int):
     _check(lib().pa_set_state(ctx, _ptr(s), int(steps_done)), "pa_set_state", ctx)
 
 
+def pa_energies(ctx, spins, n: int):
+    """Energies and cuts of host configurations (one per row), on the device."""
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    if s.ndim == 1:
+        s = s.reshape(1, -1)
+    if s.shape[1] != n:
+        raise ValueError(f"configurations must have {n} spins, got {s.shape[1]}")
+    R = s.shape[0]
+    E = np.zeros(R, np.int32)
+    cuts = np.zeros(R, np.int64)
+    _check(lib().pa_energies(ctx, _ptr(s), int(R), _ptr(E), _ptr(cuts)), "pa_energies", ctx)
+    return E, cuts
+
+
 def pa_save(ctx, path: str):
     _check(lib().pa_save(ctx, path.encode()), "pa_save", ctx)
 
@@ -269,7 +284,7 @@ def pa_step_stats(ctx, steps: int, R: int, S: int, counts: bool = False) -> dict
                 accepts=np.zeros(steps, np.int64), lnZ=np.zeros(steps),
                 sweep_emin=np.zeros((steps, max(S, 1)), np.int32),
                 nlm_pairs=np.zeros(steps, np.int32), nlm_flips=np.zeros(steps, np.int64),
-                jsel=np.zeros(steps, np.int32))
+                jsel=np.zeros(steps, np.int32), t_ms=np.zeros(steps))
     if counts:
         arrs["counts"] = np.zeros((steps, R), np.int32)
     sa = pa_step_arrays()
@@ -488,6 +503,9 @@ class Annealer:
 
     def set_state(self, spins, steps_done):
         pa_set_state(self.ctx, spins, steps_done)
+
+    def energies(self, spins):
+        return pa_energies(self.ctx, spins, self.n)
 
     def stats(self):
         return pa_stats(self.ctx)

@@ -1,58 +1,163 @@
-"""Run one anneal of a named workload and print a JSON summary.
+"""Command line: anneal a named workload or a G-set file, or verify a cut.
 
-    python -m paper_2510_21105_gb300.cli --config g63like [--steps K] [--seed S]
-        [--field-bits 16|8] [--replicas-per-cta 4|8] [--threads 512] [--hex]
+    python -m paper_2510_21105_gb300.cli [--config g63like | --graph FILE]
+        [--steps K] [--seed S] [--replicas R] [--sweeps S] [--beta LO HI K]
+        [--nlm-period P] [--variant 0|1|2] [--field-bits 16|8|7]
+        [--replicas-per-cta 4|8] [--threads T] [--hex] [--save-hex FILE]
+        [--curve FILE] [--checkpoint FILE --checkpoint-every K] [--resume FILE]
 
---steps limits the run to the first K temperature steps of the schedule
-(used for small profiling runs); --hex prints the best configuration in the
-paper's hexadecimal format.
+    python -m paper_2510_21105_gb300.cli verify --graph FILE --hex-file FILE
+        [--expect-cut C]
+
+The first form runs one anneal and prints a JSON summary; --steps limits the
+run to the first K temperature steps of the schedule (used for small
+profiling runs); --hex prints the best configuration in the paper's
+hexadecimal format (Sec. 3) and --save-hex writes it to a file. A --graph
+file is in the G-set text format ("n m", then "i j w" per edge, 1-based);
+its schedule defaults to R=16384, S=10, beta 0.1 -> 4.0 over K=1000 steps,
+non-local moves every 50 steps.
+
+For long runs, --checkpoint/--checkpoint-every save the whole anneal every K
+steps and --resume continues one (bit-exact: all randomness is counter based,
+so a resumed run equals an uninterrupted one). --curve writes the best cut
+so far at the end of every step with its device time (cut-vs-time curve).
+
+The verify form evaluates the cut of a hexadecimal configuration on the
+given graph on the device (pa_energies) and exits 1 if --expect-cut is given
+and differs.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import sys
 import time
 
+import numpy as np
 
-def main(argv=None):
+DEFAULT_FILE_SCHEDULE = dict(R=16384, S=10, beta=(0.1, 4.0), K=1000, nlm_period=50, seed=0)
+
+
+def _verify(argv):
+    from . import binding as B
+    from . import build as build_mod
+    from . import hexconfig
+    from . import workloads as wl
+
+    p = argparse.ArgumentParser(prog="cli verify")
+    p.add_argument("--graph", required=True)
+    p.add_argument("--hex-file", required=True)
+    p.add_argument("--expect-cut", type=int, default=None)
+    a = p.parse_args(argv)
+    build_mod.build()
+    g = wl.read_gset(a.graph)
+    with open(a.hex_file) as f:
+        text = "".join(line.split("#", 1)[0] for line in f)
+    x = hexconfig.decode(text, g.n)
+    with B.Annealer.from_graph(g) as ann:
+        E, cuts = ann.energies(x)
+    out = dict(graph=a.graph, n=g.n, m=g.m, energy=int(E[0]), cut=int(cuts[0]))
+    ok = a.expect_cut is None or int(cuts[0]) == a.expect_cut
+    if a.expect_cut is not None:
+        out["expected_cut"] = a.expect_cut
+        out["match"] = ok
+    print(json.dumps(out))
+    return 0 if ok else 1
+
+
+def _anneal(argv):
     from . import binding as B
     from . import build as build_mod
     from . import hexconfig
     from . import workloads as wl
 
     p = argparse.ArgumentParser()
-    p.add_argument("--config", default="g63like", choices=sorted(wl.CONFIGS))
+    src = p.add_mutually_exclusive_group()
+    src.add_argument("--config", default=None, choices=sorted(wl.CONFIGS))
+    src.add_argument("--graph", default=None)
     p.add_argument("--steps", type=int, default=None)
     p.add_argument("--seed", type=int, default=None)
+    p.add_argument("--replicas", type=int, default=None)
+    p.add_argument("--sweeps", type=int, default=None)
+    p.add_argument("--beta", type=float, nargs=3, metavar=("LO", "HI", "K"), default=None)
+    p.add_argument("--nlm-period", type=int, default=None)
     p.add_argument("--field-bits", type=int, default=0)
     p.add_argument("--replicas-per-cta", type=int, default=0)
     p.add_argument("--threads", type=int, default=0)
     p.add_argument("--variant", type=int, default=0)
     p.add_argument("--hex", action="store_true")
+    p.add_argument("--save-hex", default=None)
+    p.add_argument("--curve", default=None, help="write step,beta,t_ms,best_cut CSV")
+    p.add_argument("--checkpoint", default=None, help="checkpoint file written during the run")
+    p.add_argument("--checkpoint-every", type=int, default=0, help="steps between checkpoints")
+    p.add_argument("--resume", default=None, help="continue the anneal saved in this checkpoint")
     a = p.parse_args(argv)
     build_mod.build()
-    c = wl.CONFIGS[a.config]
-    g = c["graph"]()
+    if a.graph:
+        g = wl.read_gset(a.graph)
+        c = dict(DEFAULT_FILE_SCHEDULE)
+        name = a.graph
+    else:
+        name = a.config or "g63like"
+        c = dict(wl.CONFIGS[name])
+        g = c["graph"]()
+    if a.beta is not None:
+        c["beta"], c["K"] = (a.beta[0], a.beta[1]), int(a.beta[2])
+    for key, val in (("R", a.replicas), ("S", a.sweeps), ("nlm_period", a.nlm_period), ("seed", a.seed)):
+        if val is not None:
+            c[key] = val
     betas = wl.linear_betas(*c["beta"], c["K"])
     K = c["K"] if a.steps is None else min(a.steps, c["K"])
-    seed = c["seed"] if a.seed is None else a.seed
     with B.Annealer.from_graph(g) as ann:
         t0 = time.perf_counter()
-        ann.begin(betas, c["R"], c["S"], seed, nlm_period=c["nlm_period"], field_bits=a.field_bits,
-                  replicas_per_cta=a.replicas_per_cta, threads_per_cta=a.threads, variant=a.variant)
-        ann.run(K)
+        if a.resume:
+            ann.load(a.resume)
+            c["R"], c["S"] = ann.R, ann.S
+            K = ann.K if a.steps is None else min(a.steps, ann.K)
+            done = B.pa_run_info(ann.ctx)["steps_done"]
+        else:
+            ann.begin(betas, c["R"], c["S"], c["seed"], nlm_period=c["nlm_period"], field_bits=a.field_bits,
+                      replicas_per_cta=a.replicas_per_cta, threads_per_cta=a.threads, variant=a.variant)
+            done = 0
+        every = a.checkpoint_every if a.checkpoint and a.checkpoint_every > 0 else max(K - done, 1)
+        while done < K:
+            done = min(K, done + every)
+            ann.run(done)
+            if a.checkpoint:
+                ann.save(a.checkpoint)   # waits for the enqueued steps
         ann.sync()
         dt = time.perf_counter() - t0
         st = ann.stats()
         cut, cfg, step, sweep = ann.best()
-    out = dict(config=a.config, n=g.n, m=g.m, R=c["R"], S=c["S"], steps=K, seed=seed, best_cut=cut,
+        if a.curve:
+            ss = ann.step_stats()
+            W = st["total_weight"]
+            best = np.minimum.accumulate(ss["sweep_emin"].min(axis=1)) if len(ss["beta"]) else []
+            with open(a.curve, "w") as f:
+                f.write("step,beta,t_ms,best_cut\n")
+                for k in range(len(ss["beta"])):
+                    f.write(f"{k},{ss['beta'][k]:.17g},{ss['t_ms'][k]:.3f},{(W - int(best[k])) // 2}\n")
+    out = dict(config=name, n=g.n, m=g.m, R=c["R"], S=c["S"], steps=K, seed=c["seed"], best_cut=cut,
                best_step=step, best_sweep=sweep, wall_s=dt, attempts=st["attempts"],
                accepts=st["accepts"], device_ms=st["anneal_ms"],
                attempts_per_s=st["attempts"] / max(st["anneal_ms"], 1e-9) * 1e3)
-    if a.hex:
-        out["config_hex"] = hexconfig.encode(cfg)
+    if a.hex or a.save_hex:
+        h = hexconfig.encode(cfg)
+        if a.hex:
+            out["config_hex"] = h
+        if a.save_hex:
+            with open(a.save_hex, "w") as f:
+                f.write(h + "\n")
     print(json.dumps(out))
+    return 0
+
+
+def main(argv=None):
+    argv = sys.argv[1:] if argv is None else list(argv)
+    if argv and argv[0] == "verify":
+        return _verify(argv[1:])
+    return _anneal(argv)
 
 
 if __name__ == "__main__":
-    main()
+    sys.exit(main())

@@ -366,7 +366,10 @@ int pa_create(pa_ctx **out, int32_t n, const uint32_t *row_ptr, const uint16_t *
         ncol = std::max(ncol, k + 1);
     }
     c->ncol = ncol;
-    // Renumber: positions sorted by (colour, vertex).
+    // Renumber: positions sorted by (colour, degree descending, vertex). A colour
+    // class is an independent set and every random number is keyed by the vertex,
+    // so the order inside a class does not change any result; sorting by degree
+    // gives the 32 lanes of a warp neighbour loops of nearly equal length.
     c->cls.assign(ncol + 1, 0);
     for (int32_t i = 0; i < n; ++i) c->cls[c->colour[i] + 1]++;
     for (int32_t k = 0; k < ncol; ++k) c->cls[k + 1] += c->cls[k];
@@ -374,11 +377,12 @@ int pa_create(pa_ctx **out, int32_t n, const uint32_t *row_ptr, const uint16_t *
     c->vid.assign(n, 0);
     {
         std::vector<int32_t> fill(c->cls.begin(), c->cls.end() - 1);
-        for (int32_t i = 0; i < n; ++i) {
-            const int32_t p = fill[c->colour[i]]++;
-            c->pos[i] = p;
-            c->vid[p] = (uint32_t)i;
-        }
+        for (int32_t i = 0; i < n; ++i) c->vid[fill[c->colour[i]]++] = (uint32_t)i;
+        for (int32_t k = 0; k < ncol; ++k)
+            std::stable_sort(c->vid.begin() + c->cls[k], c->vid.begin() + c->cls[k + 1], [&](uint32_t a, uint32_t b) {
+                return row_ptr[a + 1] - row_ptr[a] > row_ptr[b + 1] - row_ptr[b];
+            });
+        for (int32_t p = 0; p < n; ++p) c->pos[c->vid[p]] = p;
     }
     c->rp_p.assign(n + 1, 0);
     c->col_p.resize(m2);
@@ -455,7 +459,7 @@ void pa_destroy(pa_ctx *ctx) {
     cudaStreamSynchronize(ctx->stream());
     free_run_events(ctx->run);
     cudaGetLastError();
-    delete ctx;   // buffers return to the pool on their own streams
+    delete ctx;   // buffers return to the memory pool
 }
 
 int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_t sweeps,
@@ -694,7 +698,7 @@ int enqueue_step(pa_ctx *c, int32_t k, cudaStream_t st, bool time_sweep) {
     sa.accepts = r.rec_acc.as<unsigned long long>();
     sa.sweep_emin = r.rec_sweep.as<int32_t>();
     cudaEvent_t s0 = nullptr, s1 = nullptr;
-    if (o.time_kernels) {
+    if (time_sweep) {
         PA_CUDA(c, cudaEventCreate(&s0));
         PA_CUDA(c, cudaEventCreate(&s1));
         r.ev_sweep.push_back(s0);
@@ -702,7 +706,7 @@ int enqueue_step(pa_ctx *c, int32_t k, cudaStream_t st, bool time_sweep) {
         PA_CUDA(c, cudaEventRecord(s0, st));
     }
     PA_CUDA(c, pa::launch_sweep(r.sweep, sa, st));
-    if (o.time_kernels) PA_CUDA(c, cudaEventRecord(s1, st));
+    if (time_sweep) PA_CUDA(c, cudaEventRecord(s1, st));
     r.launches += 1;
     r.sweep_launches += 1;
     r.cur = nxt;
@@ -971,6 +975,38 @@ int pa_set_state(pa_ctx *c, const int8_t *spins, int32_t steps_done) {
     return pa_sync(c);
 }
 
+int pa_energies(pa_ctx *c, const int8_t *spins, int32_t R, int32_t *energies, int64_t *cuts) {
+    if (!c || R < 0) return PA_EINVAL;
+    if (R == 0 || (!energies && !cuts)) return PA_OK;
+    if (!spins) return PA_EINVAL;
+    const size_t total = (size_t)R * c->n;
+    for (size_t t = 0; t < total; ++t)
+        if (spins[t] != 1 && spins[t] != -1) return fail(c, PA_EINVAL, "spins must be +1/-1");
+    // Same kernel that builds the fields and energies of a population at the
+    // start of an anneal; padding positions past n hold +1 and have no edges.
+    std::vector<int8_t> buf((size_t)R * c->np, 1);
+    for (int32_t s = 0; s < R; ++s)
+        for (int32_t i = 0; i < c->n; ++i) buf[(size_t)s * c->np + c->pos[i]] = spins[(size_t)s * c->n + i];
+    cudaStream_t st = c->stream();
+    DevBuf dx, dh, dE;
+    struct Drain {   // runs before the buffers are freed, on every return path
+        cudaStream_t s;
+        ~Drain() { cudaStreamSynchronize(s); }
+    } drain{st};
+    if (!dx.alloc(buf.size(), st) || !dh.alloc(2 * buf.size(), st) || !dE.alloc(4 * (size_t)R, st))
+        return fail(c, PA_ENOMEM, "device allocation failed");
+    std::vector<int32_t> E(R);
+    PA_CUDA(c, copy(c, dx.p, buf.data(), buf.size(), cudaMemcpyHostToDevice, st, true));
+    PA_CUDA(c, pa::launch_fields(c->gdev(), dx.as<int8_t>(), dh.as<int16_t>(), dE.as<int32_t>(), R, st));
+    PA_CUDA(c, copy(c, E.data(), dE.p, 4 * (size_t)R, cudaMemcpyDeviceToHost, st, true));
+    PA_CUDA(c, cudaStreamSynchronize(st));
+    for (int32_t s = 0; s < R; ++s) {
+        if (energies) energies[s] = E[s];
+        if (cuts) cuts[s] = (c->W - (int64_t)E[s]) / 2;
+    }
+    return PA_OK;
+}
+
 int pa_run_info(pa_ctx *c, int32_t *R, int32_t *K, int32_t *sweeps, int32_t *steps_done) {
     if (!c) return PA_EINVAL;
     const RunState &r = c->run;
@@ -1059,6 +1095,12 @@ int pa_step_stats(pa_ctx *c, pa_step_arrays *out) {
         if (!r.opts.record_counts) return fail(c, PA_ESTATE, "record_counts was off");
         PA_CUDA(c, copy(c, out->counts, r.rec_counts.p, 4 * (size_t)ks * r.R, cudaMemcpyDeviceToHost));
     }
+    if (out->t_ms) {
+        std::vector<unsigned long long> sp(r.k_done + 1);
+        PA_CUDA(c, copy(c, sp.data(), r.rec_stamp.p, 8 * (size_t)(r.k_done + 1), cudaMemcpyDeviceToHost));
+        for (int32_t k = 0; k < ks; ++k)
+            out->t_ms[k] = (sp[0] && sp[k + 1] >= sp[0]) ? (double)(sp[k + 1] - sp[0]) * 1e-6 : 0.0;
+    }
     if (out->lnZ) {
         // ln Z(beta_k) = N ln 2 + sum_{j<=k} (-dbeta_j E_min,j + ln(A_j / R))
         double lnZ = (double)c->n * std::log(2.0), prev = 0.0;
@@ -1102,6 +1144,31 @@ struct CkptHeader {
     pa_anneal_opts opts;
     int32_t best[4];
 };
+
+// Device arrays that a checkpoint carries besides the population: the
+// per-step records of the steps already run (so that statistics and curves
+// continue across a resume) and, in adaptive mode, the controller's state.
+struct RecSpec {
+    DevBuf *buf;
+    size_t per_step, extra;   // bytes = per_step * k_done + extra
+};
+
+std::vector<RecSpec> ckpt_records(RunState &r) {
+    std::vector<RecSpec> v = {{&r.rec_emin, 4, 0},      {&r.rec_A, 8, 0},
+                              {&r.rec_T, 8, 0},         {&r.rec_o, 4, 0},
+                              {&r.rec_acc, 8, 0},       {&r.rec_sweep, 4 * (size_t)r.S, 0},
+                              {&r.rec_stamp, 8, 8},     {&r.rec_nlm_pairs, 4, 0},
+                              {&r.rec_nlm_flips, 8, 0}, {&r.rec_jsel, 4, 0}};
+    if (r.opts.record_counts) v.push_back({&r.rec_counts, 4 * (size_t)r.R, 0});
+    if (r.opts.adaptive) {
+        v.push_back({&r.ad_state, 0, 16});
+        v.push_back({&r.ad_qsel, 4, 0});
+        v.push_back({&r.ad_active, 4, 0});
+        v.push_back({&r.ad_beta, 8, 0});
+        v.push_back({&r.d_tidx, 4, 0});
+    }
+    return v;
+}
 }  // namespace
 
 int pa_save(pa_ctx *c, const char *path) {
@@ -1109,7 +1176,7 @@ int pa_save(pa_ctx *c, const char *path) {
     RunState &r = c->run;
     if (!r.begun) return fail(c, PA_ESTATE, "no anneal");
     CkptHeader h{};
-    std::memcpy(h.magic, "PAMCCKP1", 8);
+    std::memcpy(h.magic, "PAMCCKP2", 8);
     h.graph_hash = c->graph_hash;
     h.n = c->n;
     h.R = r.R;
@@ -1128,6 +1195,12 @@ int pa_save(pa_ctx *c, const char *path) {
     }
     std::vector<int8_t> spins((size_t)r.R * c->n);
     if (int rc = pa_get_state(c, spins.data(), nullptr)) return rc;
+    std::vector<std::vector<char>> recs;
+    for (const RecSpec &rs : ckpt_records(r)) {
+        recs.emplace_back(rs.per_step * (size_t)r.k_done + rs.extra);
+        if (!recs.back().empty())
+            PA_CUDA(c, copy(c, recs.back().data(), rs.buf->p, recs.back().size(), cudaMemcpyDeviceToHost));
+    }
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(c, PA_EINVAL, "cannot open checkpoint for writing");
     bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1;
@@ -1136,6 +1209,7 @@ int pa_save(pa_ctx *c, const char *path) {
     if (nb) ok = ok && std::fwrite(r.betas.data(), 8, nb, f) == (size_t)nb;
     ok = ok && std::fwrite(cfg.data(), 1, cfg.size(), f) == cfg.size();
     ok = ok && std::fwrite(spins.data(), 1, spins.size(), f) == spins.size();
+    for (const auto &b : recs) ok = ok && (b.empty() || std::fwrite(b.data(), 1, b.size(), f) == b.size());
     std::fclose(f);
     return ok ? PA_OK : fail(c, PA_EINVAL, "checkpoint write failed");
 }
@@ -1146,7 +1220,7 @@ int pa_load(pa_ctx *c, const char *path) {
     if (!f) return fail(c, PA_EINVAL, "cannot open checkpoint");
     CkptHeader h{};
     int32_t nb = 0;
-    bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, "PAMCCKP1", 8) == 0 &&
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, "PAMCCKP2", 8) == 0 &&
               std::fread(&nb, 4, 1, f) == 1 && nb >= 0 && nb <= (1 << 26);
     if (!ok || h.graph_hash != c->graph_hash || h.n != c->n) {
         std::fclose(f);
@@ -1157,12 +1231,29 @@ int pa_load(pa_ctx *c, const char *path) {
     ok = (nb == 0 || std::fread(betas.data(), 8, nb, f) == (size_t)nb) &&
          std::fread(cfg.data(), 1, cfg.size(), f) == cfg.size() &&
          std::fread(spins.data(), 1, spins.size(), f) == spins.size();
-    std::fclose(f);
-    if (!ok) return fail(c, PA_EINVAL, "truncated checkpoint");
+    if (!ok || h.k_done < 0 || h.k_done > h.K) {
+        std::fclose(f);
+        return fail(c, PA_EINVAL, "truncated checkpoint");
+    }
     pa_anneal_opts o = h.opts;
     o.stream = c->run.opts.stream;
     int rc = pa_anneal_begin(c, nb ? betas.data() : nullptr, h.K, h.R, h.S, h.seed, &o);
-    if (rc) return rc;
+    if (rc) {
+        std::fclose(f);
+        return rc;
+    }
+    const std::vector<RecSpec> specs = ckpt_records(c->run);
+    std::vector<std::vector<char>> recs;
+    for (const RecSpec &rs : specs) {
+        recs.emplace_back(rs.per_step * (size_t)h.k_done + rs.extra);
+        if (!recs.back().empty()) ok = ok && std::fread(recs.back().data(), 1, recs.back().size(), f) == recs.back().size();
+    }
+    std::fclose(f);
+    if (!ok) return fail(c, PA_EINVAL, "truncated checkpoint");
+    if ((rc = pa_sync(c))) return rc;   // the clears that pa_anneal_begin enqueued come first
+    for (size_t i = 0; i < specs.size(); ++i)
+        if (!recs[i].empty())
+            PA_CUDA(c, copy(c, specs[i].buf->p, recs[i].data(), recs[i].size(), cudaMemcpyHostToDevice));
     if ((rc = pa_set_state(c, spins.data(), h.k_done))) return rc;
     if (h.best[1] >= 0) {
         // The restored best goes into the record of block 0 with its configuration; later

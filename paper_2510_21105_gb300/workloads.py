@@ -23,6 +23,7 @@ rows and each row sorted by neighbour index.
 """
 from __future__ import annotations
 
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -157,6 +158,36 @@ def delaunay(n: int, seed: int = 0) -> Graph:
     e.sort(axis=1)
     e = np.unique(e, axis=0)
     return from_edges(n, e[:, 0], e[:, 1], name=f"delaunay{n}_s{seed}")
+
+
+def read_gset(path: str, name: str = "") -> Graph:
+    """Graph from a G-set style text file: a header line "n m", then m lines
+    "i j w" with 1-based vertices and w = +1 or -1 (the benchmark format of
+    the graphs named in Sec. 1)."""
+    with open(path) as f:
+        head = f.readline().split()
+        if len(head) < 2:
+            raise ValueError(f"{path}: header must be 'n m'")
+        n, m = int(head[0]), int(head[1])
+        rows = np.loadtxt(f, dtype=np.int64, ndmin=2) if m else np.zeros((0, 3), np.int64)
+    if rows.shape != (m, 3):
+        raise ValueError(f"{path}: expected {m} lines of 'i j w', found shape {rows.shape}")
+    i, j, w = rows[:, 0] - 1, rows[:, 1] - 1, rows[:, 2]
+    if m and (i.min() < 0 or j.min() < 0 or i.max() >= n or j.max() >= n):
+        raise ValueError(f"{path}: vertex index out of 1..{n}")
+    if np.any((w != 1) & (w != -1)):
+        raise ValueError(f"{path}: weights must be +1 or -1")
+    return from_edges(n, i, j, None if np.all(w == 1) else w.astype(np.int8),
+                      name=name or os.path.basename(path))
+
+
+def write_gset(g: Graph, path: str) -> None:
+    """Write g in the format read_gset reads (each edge once, i < j)."""
+    i, j, w = g.edges()
+    with open(path, "w") as f:
+        f.write(f"{g.n} {len(i)}\n")
+        for a, b, c in zip(i.tolist(), j.tolist(), w.tolist()):
+            f.write(f"{a + 1} {b + 1} {c}\n")
 
 
 def linear_betas(lo: float, hi: float, K: int) -> np.ndarray:

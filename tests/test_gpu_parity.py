@@ -131,26 +131,41 @@ def test_degenerate_cases():
     a.close()
 
 
-def test_checkpoint_resume_is_bit_exact(tmp_path):
+@pytest.mark.parametrize("kw,K,split", [
+    (dict(nlm_period=4), 10, 6),
+    (dict(variant=1), 10, 3),
+    (dict(adaptive=1, rho=0.5, adapt_J=4, adapt_dbeta_max=0.3, beta_max=1.5, nlm_period=3), 40, 7),
+], ids=["fixed-nlm", "msc", "adaptive"])
+def test_checkpoint_resume_is_bit_exact(tmp_path, kw, K, split):
+    """A run saved after `split` steps and resumed in a fresh context equals
+    the uninterrupted run: population, best record and every per-step record
+    (the adaptive controller's state travels in the checkpoint)."""
+    require_gpu()
     g = wl.gnp(200, 0.05, seed=21)
-    betas = wl.linear_betas(0.1, 2.5, 10)
+    betas = None if kw.get("adaptive") else wl.linear_betas(0.1, 2.5, K)
     full = B.Annealer.from_graph(g)
-    full.anneal(betas, R=32, S=3, seed=5, nlm_period=4)
+    full.anneal(betas, R=64, S=3, seed=5, K=K, **kw)
     s_full, E_full = full.state()
     b_full = full.best_record()
+    st_full = full.step_stats()
     part = B.Annealer.from_graph(g)
-    part.begin(betas, R=32, S=3, seed=5, nlm_period=4)
-    part.run(6)
+    part.begin(betas, R=64, S=3, seed=5, K=K, **kw)
+    part.run(split)
     part.sync()
     part.save(str(tmp_path / "ck.bin"))
     part.close()
     res = B.Annealer.from_graph(g)
     res.load(str(tmp_path / "ck.bin"))
-    res.run(10)
+    res.run(K)
     res.sync()
     s_res, E_res = res.state()
     assert np.array_equal(s_full, s_res) and np.array_equal(E_full, E_res)
     assert res.best_record() == b_full
+    st_res = res.step_stats()
+    assert len(st_res["beta"]) == len(st_full["beta"]) > split
+    for key in ("beta", "emin", "A", "T", "o", "accepts", "sweep_emin", "nlm_pairs", "nlm_flips", "jsel", "lnZ"):
+        assert np.array_equal(st_full[key], st_res[key]), key
+    assert np.all(np.diff(st_res["t_ms"]) >= 0) and st_res["t_ms"][-1] > 0
     full.close()
     res.close()
 
@@ -166,3 +181,14 @@ def test_repeat_runs_are_identical_and_launch_shape_free():
     r6 = run_gpu(g, betas, 64, 3, seed=77, variant=1)
     for r in (r2, r3, r4, r5, r6):
         assert np.array_equal(r1["spins"], r["spins"]) and r1["best"] == r["best"]
+
+
+def test_parity_msc_many_words_ragged_last_word():
+    # R = 4937: 155 words of 32 replicas (more words than SMs, so blocks loop
+    # over words) with 9 live replicas in the last one; signed weights and
+    # non-local moves.
+    g = wl.from_edges(300, *_random_edges(300, 1500, seed=99))
+    betas = wl.linear_betas(0.1, 2.5, 6)
+    gpu = run_gpu(g, betas, 4937, 2, seed=31, variant=1, nlm_period=2)
+    orc = run_oracle(g, betas, 4937, 2, seed=31, nlm_period=2)
+    assert_parity(gpu, orc, g, 4937, 2)
