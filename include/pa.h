@@ -58,7 +58,7 @@ typedef struct pa_ctx pa_ctx;
 #define PA_VARIANT_AUTO 2 /* chosen per graph by the built-in tuning table */
 
 typedef struct {
-    int32_t variant;          /* PA_VARIANT_*; default PA_VARIANT_I8 */
+    int32_t variant;          /* PA_VARIANT_*; default PA_VARIANT_AUTO */
     int32_t field_bits;       /* I8 variant: shared-memory layout of a replica
                                  block: 16 = int8 spin + int16 field,
                                  8 = int8 spin + int8 field, 7 = one packed
@@ -70,7 +70,11 @@ typedef struct {
                                  step k when k > 0 and k % nlm_period == 0;
                                  0 = off (default) */
     int32_t adaptive;         /* 0 = schedule from betas[] (default);
-                                 1 = ESS-adaptive temperature steps */
+                                 1 = ESS-adaptive temperature steps;
+                                 2 = acceptance-rate-adaptive steps (same
+                                 grid; the level moves one finer after a
+                                 step that accepted less than acc_lo of its
+                                 attempts, one coarser above acc_hi) */
     double rho;               /* adaptive: target ESS / R, in (0, 1] */
     int32_t adapt_J;          /* adaptive: finest level J (0..20) */
     double adapt_dbeta_max;   /* adaptive: coarsest step dbeta_max > 0 */
@@ -81,6 +85,27 @@ typedef struct {
                                  NULL = the legacy default stream */
     int32_t record_counts;    /* 1 = keep per-step copy counts (steps x R) */
     int32_t time_kernels;     /* 1 = time every sweep launch with CUDA events */
+    int32_t nlm_kind;         /* non-local move (Sec. 3 names the moves only):
+                                 0 = Houdayer cluster exchange between random
+                                 replica pairs (default); 1 = block move: each
+                                 replica flips the first nlm_block vertices of
+                                 a breadth-first search from a random seed
+                                 (rows scanned in CSR order) as one Metropolis
+                                 move, accepted iff m <= 0 or u < A(m) with
+                                 A(m) = min(2^32-1, floor(2^32 q^m)),
+                                 q = exp(-2 beta_k) and m half the energy change */
+    int32_t nlm_block;        /* block move size b, 1..1024 (default 32) */
+    double acc_lo, acc_hi;    /* adaptive = 2: acceptance-rate band,
+                                 0 <= acc_lo <= acc_hi <= 1 (0.05, 0.25) */
+    int32_t reheat_after;     /* fixed schedules only: stagnation reheating.
+                                 The schedule index advances one entry per
+                                 step (staying at the last) unless this many
+                                 consecutive steps found no lower energy at
+                                 their sweep ends; then it steps back
+                                 reheat_back entries (not below 0). Steps that
+                                 do not advance resample with q = 1 (identity).
+                                 0 = off (default) */
+    int32_t reheat_back;      /* entries a reheat steps back (>= 1) */
 } pa_anneal_opts;
 
 typedef struct {
@@ -112,9 +137,11 @@ typedef struct {
     int64_t *accepts;         /* accepted flips in the sweeps of step k */
     double *lnZ;              /* free-energy estimate ln Z(beta_k) */
     int32_t *sweep_emin;      /* minimum energy over replicas after each sweep */
-    int32_t *nlm_pairs;       /* non-local moves performed (pairs with D != {}) */
+    int32_t *nlm_pairs;       /* non-local moves performed: pairs with D != {}
+                                 (Houdayer) or accepted moves (block) */
     int64_t *nlm_flips;       /* spins flipped per replica by those moves */
-    int32_t *jsel;            /* adaptive: chosen level j (-1 otherwise) */
+    int32_t *jsel;            /* adaptive: chosen level j; reheating: the
+                                 schedule index of step k; -1 otherwise */
     int32_t *counts;          /* copy counts n_r (record_counts = 1) */
     double *t_ms;             /* device time from the start of step 0 to the
                                  end of step k (global timer; includes any

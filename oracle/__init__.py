@@ -39,7 +39,9 @@ def build(force: bool = False) -> str:
 
 class OrcOpts(C.Structure):
     _fields_ = [("nlm_period", C.c_int32), ("adaptive", C.c_int32), ("rho", C.c_double),
-                ("adapt_J", C.c_int32), ("adapt_dbeta_max", C.c_double), ("beta_max", C.c_double)]
+                ("adapt_J", C.c_int32), ("adapt_dbeta_max", C.c_double), ("beta_max", C.c_double),
+                ("nlm_kind", C.c_int32), ("nlm_block", C.c_int32), ("acc_lo", C.c_double),
+                ("acc_hi", C.c_double), ("reheat_after", C.c_int32), ("reheat_back", C.c_int32)]
 
 
 class OrcOut(C.Structure):
@@ -75,8 +77,10 @@ def lib():
             L.orc_anneal.argtypes = [i32, vp, vp, vp, vp, i32, i32, i32, u64, C.POINTER(OrcOpts),
                                      C.POINTER(OrcOut)]
             L.orc_anneal.restype = C.c_int
-            L.orc_step.argtypes = [i32, vp, vp, vp, i32, i32, u64, i32, dbl, dbl, i32, vp, i32, vp,
-                                   vp, vp, vp, vp]
+            L.orc_step.argtypes = [i32, vp, vp, vp, i32, i32, u64, i32, dbl, dbl, i32, i32, vp, i32,
+                                   vp, vp, vp, vp, vp]
+            L.orc_block_move.argtypes = [i32, vp, vp, vp, vp, vp, i32, dbl, i32, C.c_uint32, vp]
+            L.orc_block_move.restype = i32
             L.orc_step.restype = C.c_int
         return _lib
 
@@ -150,6 +154,19 @@ def houdayer_pair(rp, col, xa, xb, u: int):
     return int(size), xa, xb, cl.astype(bool)
 
 
+def block_move(rp, col, w, x, E: int, b: int, q: float, seed_vertex: int, u: int):
+    """One block move on a copy of x (``orc_block_move``): returns (size
+    flipped or 0, new spins, new energy, block mask)."""
+    rp, col, w = _graph_arrays(rp, col, w)
+    x = np.array(x, dtype=np.int8)
+    n = len(rp) - 1
+    e = C.c_int32(int(E))
+    mask = np.zeros(n, np.uint8)
+    size = lib().orc_block_move(n, _p(rp), _p(col), _p(w), _p(x), C.byref(e), int(b), float(q),
+                                int(seed_vertex), int(u), _p(mask))
+    return int(size), x, int(e.value), mask.astype(bool)
+
+
 def nlm_order(R: int, seed: int, k: int):
     order = np.zeros(R, np.int32)
     lib().orc_nlm_order(int(R), int(seed), int(k), _p(order))
@@ -181,8 +198,10 @@ class AnnealResult:
 
 
 def anneal(rp, col, w, betas, R: int, S: int, seed: int, *, K: int | None = None,
-           nlm_period: int = 0, adaptive: bool = False, rho: float = 0.5, adapt_J: int = 8,
-           adapt_dbeta_max: float = 0.05, beta_max: float = 0.0, record_counts: bool = False):
+           nlm_period: int = 0, adaptive: int = 0, rho: float = 0.5, adapt_J: int = 8,
+           adapt_dbeta_max: float = 0.05, beta_max: float = 0.0, record_counts: bool = False,
+           nlm_kind: int = 0, nlm_block: int = 1, acc_lo: float = 0.0, acc_hi: float = 1.0,
+           reheat_after: int = 0, reheat_back: int = 0):
     """Run the oracle PAMC (see ``orc_anneal`` in pamc_oracle.c)."""
     rp, col, w = _graph_arrays(rp, col, w)
     n = len(rp) - 1
@@ -193,8 +212,9 @@ def anneal(rp, col, w, betas, R: int, S: int, seed: int, *, K: int | None = None
     else:
         b = np.ascontiguousarray(betas, dtype=np.float64)
         K = len(b) if K is None else K
-    opts = OrcOpts(int(nlm_period), int(bool(adaptive)), float(rho), int(adapt_J),
-                   float(adapt_dbeta_max), float(beta_max))
+    opts = OrcOpts(int(nlm_period), int(adaptive), float(rho), int(adapt_J),
+                   float(adapt_dbeta_max), float(beta_max), int(nlm_kind), int(nlm_block), float(acc_lo),
+                   float(acc_hi), int(reheat_after), int(reheat_back))
     arr = dict(
         spins=np.zeros((R, n), np.int8), E=np.zeros(R, np.int32), step_beta=np.zeros(K),
         step_emin=np.zeros(K, np.int32), step_A=np.zeros(K), step_T=np.zeros(K, np.uint64),
@@ -225,7 +245,7 @@ def anneal(rp, col, w, betas, R: int, S: int, seed: int, *, K: int | None = None
 
 
 def step_replay(rp, col, w, spins_in, S: int, seed: int, k: int, beta_prev: float, beta_k: float,
-                subset, nlm_now: bool = False, want_counts: bool = True):
+                subset, nlm_now: bool = False, want_counts: bool = True, nlm_block: int = 0):
     """Replay temperature step k for the listed new slots (``orc_step``)."""
     rp, col, w = _graph_arrays(rp, col, w)
     spins_in = np.ascontiguousarray(spins_in, dtype=np.int8)
@@ -236,7 +256,8 @@ def step_replay(rp, col, w, spins_in, S: int, seed: int, k: int, beta_prev: floa
     counts = np.zeros(R, np.int32) if want_counts else None
     acc = C.c_int64()
     rc = lib().orc_step(n, _p(rp), _p(col), _p(w), R, int(S), int(seed), int(k), float(beta_prev),
-                        float(beta_k), int(bool(nlm_now)), _p(spins_in), len(sub), _p(sub), _p(out),
+                        float(beta_k), int(bool(nlm_now)), int(nlm_block), _p(spins_in), len(sub),
+                        _p(sub), _p(out),
                         _p(E), _p(counts), C.byref(acc))
     if rc != 0:
         raise ValueError(f"orc_step failed (rc={rc})")

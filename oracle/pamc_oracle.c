@@ -40,11 +40,21 @@
  *                       final energies equal full recomputation
  *   orc_houdayer_pair   cluster = networkx connected component of the seed in
  *                       G[D]; E_a + E_b invariant
+ *   orc_block_move      block = the first b vertices of a networkx BFS that
+ *                       visits neighbours in row order; m = half the energy
+ *                       change computed by full recomputation; brute-force
+ *                       acceptance frequency against min(1, exp(-2 beta m))
  *   adaptive mode       chosen step meets ESS >= rho R unless it is the
  *                       finest; beta monotone and ends at beta_max
+ *   adaptive = 2        level sequence recomputed from the recorded accepted
+ *                       flips; beta monotone, ends at beta_max
+ *   reheating           schedule index sequence recomputed from the recorded
+ *                       sweep minima; non-advancing steps resample as the
+ *                       identity
  * Parity against the paper itself is unpinned for every step the paper does
  * not define (Sec. 3-4): sweep order, acceptance rule, resampling scheme,
- * adaptive control and non-local moves.
+ * adaptive control (ESS rule, acceptance-rate rule, stagnation reheating)
+ * and non-local moves (Houdayer pairs, block moves).
  */
 #include <math.h>
 #include <stdint.h>
@@ -330,16 +340,94 @@ static uint32_t nlm_seed_word(uint64_t seed, int32_t k, int32_t m)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Block move (alternative reading of the non-local moves, nlm_kind = 1):    */
+/* one replica flips a connected block of up to b spins as a single         */
+/* Metropolis move.                                                          */
+/*   B    the first b vertices reached by breadth-first search from the      */
+/*        seed vertex, each row scanned in CSR order (fewer when the seed's  */
+/*        component is smaller);                                             */
+/*   m    half the energy change of flipping B: only the edges leaving B     */
+/*        change sign, so m = -sum_{i in B, j not in B} w_ij x_i x_j;        */
+/*   rule accept iff m <= 0 or u < A(m), A(m) = min(2^32 - 1,                */
+/*        floor(2^32 q^m)) with q = exp(-2 beta) and q^m by square and       */
+/*        multiply (the same power as the resampling weights).              */
+/* Returns |B| if the move is accepted (x flipped on B, *E += 2m), else 0.   */
+/* block (may be NULL) receives the 0/1 mask of B either way.               */
+/* ------------------------------------------------------------------------ */
+int32_t orc_block_move(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w,
+                       int8_t *x, int32_t *E, int32_t b, double q, int32_t seedv, uint32_t u,
+                       uint8_t *block)
+{
+    if (n < 1 || b < 1 || seedv < 0 || seedv >= n) return 0;
+    uint8_t *in = (uint8_t *)calloc((size_t)n, 1);
+    int32_t *queue = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    int32_t head = 0, tail = 0;
+    in[seedv] = 1;
+    queue[tail++] = seedv;
+    while (head < tail && tail < b) {
+        int32_t i = queue[head++];
+        for (int64_t e = rp[i]; e < rp[i + 1] && tail < b; ++e) {
+            int32_t j = col[e];
+            if (!in[j]) { in[j] = 1; queue[tail++] = j; }
+        }
+    }
+    int64_t leaving = 0;                 /* sum over edges leaving B of w x_i x_j */
+    for (int32_t h = 0; h < tail; ++h) {
+        int32_t i = queue[h];
+        for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+            int32_t j = col[e];
+            if (!in[j]) leaving += (int64_t)(w ? w[e] : 1) * x[i] * x[j];
+        }
+    }
+    int64_t m = -leaving;
+    int accept = m <= 0;
+    if (!accept) {
+        double v = floor(ldexp(power_sq_mul(q, (uint32_t)m), 32));
+        uint32_t A = v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
+        accept = u < A;
+    }
+    if (block) for (int32_t i = 0; i < n; ++i) block[i] = in[i];
+    if (accept) {
+        for (int32_t h = 0; h < tail; ++h) x[queue[h]] = (int8_t)-x[queue[h]];
+        *E += (int32_t)(2 * m);
+    }
+    free(in);
+    free(queue);
+    return accept ? tail : 0;
+}
+
+/* Random words of the block move of slot r at step k: the seed vertex is
+ * word r&3 of Philox((r>>2, 2, k, tag 2)) mod n and the acceptance word is
+ * word r&3 of Philox((r>>2, 3, k, tag 2)). */
+static int32_t block_seed_vertex(uint64_t seed, int32_t k, int32_t r, int32_t n)
+{
+    return (int32_t)(rng_word(seed, (uint32_t)r >> 2, 2, (uint32_t)k, (uint32_t)TAG_NONLOCAL << 28, r & 3) %
+                     (uint32_t)n);
+}
+
+static uint32_t block_accept_word(uint64_t seed, int32_t k, int32_t r)
+{
+    return rng_word(seed, (uint32_t)r >> 2, 3, (uint32_t)k, (uint32_t)TAG_NONLOCAL << 28, r & 3);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Full anneal.                                                              */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int32_t nlm_period;       /* non-local move after the sweeps of step k when
                                  k > 0 and k % nlm_period == 0; 0 = off */
-    int32_t adaptive;         /* 0: betas[] is the schedule; 1: ESS-adaptive */
+    int32_t adaptive;         /* 0: betas[] is the schedule; 1: ESS-adaptive;
+                                 2: acceptance-rate-adaptive */
     double rho;               /* adaptive: ESS / R threshold */
     int32_t adapt_J;          /* adaptive: finest grid level J */
     double adapt_dbeta_max;   /* adaptive: coarsest step */
     double beta_max;          /* adaptive: final inverse temperature */
+    int32_t nlm_kind;         /* 0: Houdayer pair moves; 1: block moves */
+    int32_t nlm_block;        /* block moves: block size b >= 1 */
+    double acc_lo, acc_hi;    /* adaptive = 2: acceptance-rate band */
+    int32_t reheat_after;     /* fixed schedules: reheat after this many steps
+                                 without a new best energy; 0 = off */
+    int32_t reheat_back;      /* schedule entries a reheat steps back */
 } orc_opts;
 
 typedef struct {              /* every pointer may be NULL */
@@ -354,9 +442,12 @@ typedef struct {              /* every pointer may be NULL */
     double *step_lnZ;         /* [K] free-energy estimate ln Z(beta_k) */
     int32_t *step_counts;     /* [K][R] copy counts of step k */
     int32_t *step_sweep_emin; /* [K][S] min energy over replicas after each sweep */
-    int32_t *step_nlm_pairs;  /* [K] pairs with a non-empty D */
-    int64_t *step_nlm_flips;  /* [K] sum of cluster sizes */
-    int32_t *step_jsel;       /* [K] adaptive: chosen grid level */
+    int32_t *step_nlm_pairs;  /* [K] pairs with a non-empty D (block moves:
+                                 accepted moves) */
+    int64_t *step_nlm_flips;  /* [K] sum of cluster sizes (block moves: spins
+                                 flipped by accepted moves) */
+    int32_t *step_jsel;       /* [K] adaptive: chosen grid level; reheating:
+                                 schedule index used by step k */
     int8_t *best_config;      /* [n] configuration of the best energy */
     int32_t best[4];          /* best energy, step, sweep, slot (-1 if none) */
     int32_t steps_run;
@@ -483,6 +574,23 @@ static void nonlocal_moves(const graph_view *g, int8_t *pop, int32_t *E, int32_t
     if (flips_out) *flips_out = flips;
 }
 
+/* Block moves of step k: every slot independently (see orc_block_move). */
+static void block_moves(const graph_view *g, int8_t *pop, int32_t *E, int32_t R, uint64_t seed,
+                        int32_t k, int32_t b, double beta_k, int32_t *moves_out, int64_t *flips_out)
+{
+    const double q = exp(-2.0 * beta_k);
+    int32_t moves = 0;
+    int64_t flips = 0;
+    for (int32_t r = 0; r < R; ++r) {
+        int32_t size = orc_block_move(g->n, g->rp, g->col, g->w, pop + (size_t)r * g->n, &E[r], b, q,
+                                      block_seed_vertex(seed, k, r, g->n), block_accept_word(seed, k, r),
+                                      NULL);
+        if (size > 0) { ++moves; flips += size; }
+    }
+    if (moves_out) *moves_out = moves;
+    if (flips_out) *flips_out = flips;
+}
+
 /* Adaptive step choice (reading of "adaptive control of stochasticity"):
  * beta moves on the grid beta = n * delta, delta = dbeta_max / 2^J. From
  * the current grid index n_prev, level j proposes dn_j = 2^(J-j) (clamped
@@ -529,16 +637,19 @@ int orc_anneal(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w
                const orc_opts *opts, orc_out *out)
 {
     if (n < 1 || K < 0 || R < 1 || S < 0) return -1;
-    orc_opts o = {0, 0, 0.0, 0, 0.0, 0.0};
+    orc_opts o = {0, 0, 0.0, 0, 0.0, 0.0, 0, 1, 0.0, 1.0, 0, 0};
     if (opts) o = *opts;
+    if (o.nlm_kind < 0 || o.nlm_kind > 1 || (o.nlm_kind == 1 && o.nlm_block < 1)) return -1;
+    if (o.reheat_after < 0 || (o.reheat_after > 0 && (o.adaptive || o.reheat_back < 1))) return -1;
     if (!o.adaptive) {
         double prev = 0.0;
         for (int32_t k = 0; k < K; ++k) {
             if (!isfinite(betas[k]) || betas[k] < prev) return -1;
             prev = betas[k];
         }
-    } else if (o.adapt_J < 0 || o.adapt_J > 20 || !(o.adapt_dbeta_max > 0.0) ||
-               !(o.beta_max >= 0.0) || !isfinite(o.beta_max)) {
+    } else if (o.adaptive < 0 || o.adaptive > 2 || o.adapt_J < 0 || o.adapt_J > 20 ||
+               !(o.adapt_dbeta_max > 0.0) || !(o.beta_max >= 0.0) || !isfinite(o.beta_max) ||
+               (o.adaptive == 2 && !(o.acc_lo >= 0.0 && o.acc_lo <= o.acc_hi && o.acc_hi <= 1.0))) {
         return -1;
     }
     graph_view g;
@@ -556,6 +667,11 @@ int orc_anneal(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w
     int32_t n_max = o.adaptive ? (int32_t)floor(o.beta_max / delta + 0.5) : 0;
     double rhoR = o.rho * (double)R;
     int32_t n_prev = 0;
+    int32_t j_prev = 0;                 /* adaptive = 2: current level */
+    int64_t acc_prev = 0;               /* accepted flips of the previous step */
+    int32_t i_prev = 0, stall = 0;      /* reheating: schedule index, steps without a new best */
+    int32_t best_run = 0x7FFFFFFF, step_min = 0x7FFFFFFF;
+    const double attempts = (double)((int64_t)n * R * S);
 
     double beta_prev = 0.0;
     double lnZ = (double)n * log(2.0);
@@ -565,12 +681,53 @@ int orc_anneal(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w
         double beta_k, q;
         if (o.adaptive) {
             if (n_prev >= n_max) break;
-            int32_t jsel;
-            int32_t dn = adaptive_choose(E, R, n_prev, n_max, o.adapt_J, delta, rhoR, &jsel);
+            int32_t jsel, dn;
+            if (o.adaptive == 2) {
+                /* Acceptance-rate control (alternative reading of the adaptive
+                 * stochasticity): a previous step that accepted fewer than
+                 * acc_lo of its attempts refines the temperature step by one
+                 * level (dn halves), more than acc_hi coarsens it by one. */
+                if (k > 0) {
+                    if ((double)acc_prev < o.acc_lo * attempts) {
+                        if (j_prev < o.adapt_J) ++j_prev;
+                    } else if ((double)acc_prev > o.acc_hi * attempts) {
+                        if (j_prev > 0) --j_prev;
+                    }
+                }
+                jsel = j_prev;
+                dn = 1 << (o.adapt_J - j_prev);
+                if (dn > n_max - n_prev) dn = n_max - n_prev;
+            } else {
+                dn = adaptive_choose(E, R, n_prev, n_max, o.adapt_J, delta, rhoR, &jsel);
+            }
             if (out->step_jsel) out->step_jsel[k] = jsel;
             n_prev += dn;
             beta_k = (double)n_prev * delta;
             q = exp(-((double)dn * delta));
+        } else if (o.reheat_after > 0) {
+            /* Stagnation reheating (alternative reading of the adaptive
+             * stochasticity): the schedule index advances by one per step
+             * (and stays at the last entry) unless reheat_after consecutive
+             * steps found no lower energy at their sweep ends; then it steps
+             * back by reheat_back entries (not below 0) and the count
+             * restarts. A step that does not advance the index leaves the
+             * population unweighted (q = 1, identity resampling). */
+            int32_t i = 0, forward = 1;
+            if (k > 0) {
+                if (step_min < best_run) { best_run = step_min; stall = 0; }
+                else ++stall;
+                if (stall >= o.reheat_after) {
+                    i = i_prev - o.reheat_back < 0 ? 0 : i_prev - o.reheat_back;
+                    stall = 0;
+                } else {
+                    i = i_prev + 1 < K ? i_prev + 1 : K - 1;
+                }
+                forward = i == i_prev + 1;
+            }
+            if (out->step_jsel) out->step_jsel[k] = i;
+            beta_k = betas[i];
+            q = forward ? exp(-(betas[i] - (i > 0 ? betas[i - 1] : 0.0))) : 1.0;
+            i_prev = i;
         } else {
             beta_k = betas[k];
             q = exp(-(beta_k - beta_prev));
@@ -593,6 +750,7 @@ int orc_anneal(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w
 
         orc_accept_table(beta_k, g.maxdeg, T);
         int64_t acc = 0;
+        step_min = 0x7FFFFFFF;
         for (int32_t s = 0; s < S; ++s) {
             int32_t sweep_min = 0x7FFFFFFF;
             for (int32_t r = 0; r < R; ++r)
@@ -605,13 +763,19 @@ int orc_anneal(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w
                 }
             }
             if (out->step_sweep_emin) out->step_sweep_emin[(size_t)k * S + s] = sweep_min;
+            if (sweep_min < step_min) step_min = sweep_min;
         }
         if (out->step_accepts) out->step_accepts[k] = acc;
+        acc_prev = acc;
 
         int32_t pairs = 0;
         int64_t flips = 0;
-        if (o.nlm_period > 0 && k > 0 && k % o.nlm_period == 0)
-            nonlocal_moves(&g, pop, E, R, seed, k, &pairs, &flips);
+        if (o.nlm_period > 0 && k > 0 && k % o.nlm_period == 0) {
+            if (o.nlm_kind == 1)
+                block_moves(&g, pop, E, R, seed, k, o.nlm_block, beta_k, &pairs, &flips);
+            else
+                nonlocal_moves(&g, pop, E, R, seed, k, &pairs, &flips);
+        }
         if (out->step_nlm_pairs) out->step_nlm_pairs[k] = pairs;
         if (out->step_nlm_flips) out->step_nlm_flips[k] = flips;
         beta_prev = beta_k;
@@ -633,17 +797,20 @@ int orc_anneal(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w
  * recomputed, the population is resampled from beta_prev to beta_k, each
  * listed slot takes its parent's configuration and runs S sweeps at beta_k,
  * and, when nlm_now is set, listed pairs of the step-k pairing get the
- * non-local move. The subset must contain both members of every pair it
- * touches when nlm_now is set. Outputs the listed slots' spins [nsub][n] and
+ * non-local move (nlm_block = 0) or every listed slot gets its block move of
+ * size nlm_block (nlm_block >= 1). For pair moves the subset must contain
+ * both members of every pair it touches. Outputs the listed slots' spins [nsub][n] and
  * energies, the accepted flips summed over the listed slots, and optionally
  * the copy counts [R]. Returns 0, -1 on invalid arguments, -3 if a pair is
  * split by the subset. */
 int orc_step(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w,
              int32_t R, int32_t S, uint64_t seed, int32_t k, double beta_prev, double beta_k,
-             int32_t nlm_now, const int8_t *spins_in, int32_t nsub, const int32_t *sub,
-             int8_t *spins_out, int32_t *E_out, int32_t *counts, int64_t *accepts_out)
+             int32_t nlm_now, int32_t nlm_block, const int8_t *spins_in, int32_t nsub,
+             const int32_t *sub, int8_t *spins_out, int32_t *E_out, int32_t *counts,
+             int64_t *accepts_out)
 {
-    if (n < 1 || R < 1 || S < 0 || !(beta_k >= beta_prev) || !isfinite(beta_k)) return -1;
+    if (n < 1 || R < 1 || S < 0 || !(beta_k >= beta_prev) || !isfinite(beta_k) || nlm_block < 0)
+        return -1;
     graph_view g;
     build_view(&g, n, rp, col, w);
     int32_t *E = (int32_t *)malloc((size_t)R * sizeof(int32_t));
@@ -665,7 +832,12 @@ int orc_step(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w,
     for (int32_t sw = 0; sw < S; ++sw)
         for (int32_t q = 0; q < nsub; ++q)
             acc += sweep_replica(&g, spins_out + (size_t)q * n, &E_out[q], T, seed, sub[q], k, sw);
-    if (nlm_now) {
+    if (nlm_now && nlm_block > 0) {
+        const double qb = exp(-2.0 * beta_k);
+        for (int32_t q = 0; q < nsub; ++q)
+            orc_block_move(n, rp, col, w, spins_out + (size_t)q * n, &E_out[q], nlm_block, qb,
+                           block_seed_vertex(seed, k, sub[q], n), block_accept_word(seed, k, sub[q]), NULL);
+    } else if (nlm_now) {
         int32_t *order = (int32_t *)malloc((size_t)R * sizeof(int32_t));
         int32_t *where = (int32_t *)malloc((size_t)R * sizeof(int32_t));
         orc_nlm_order(R, seed, k, order);

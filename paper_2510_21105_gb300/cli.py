@@ -2,7 +2,7 @@
 
     python -m paper_2510_21105_gb300.cli [--config g63like | --graph FILE]
         [--steps K] [--seed S] [--replicas R] [--sweeps S] [--beta LO HI K]
-        [--nlm-period P] [--variant 0|1|2] [--field-bits 16|8|7]
+        [--nlm-period P] [--nlm-kind 0|1] [--nlm-block B] [--variant 0|1|2] [--field-bits 16|8|7]
         [--replicas-per-cta 4|8] [--threads T] [--hex] [--save-hex FILE]
         [--curve FILE] [--checkpoint FILE --checkpoint-every K] [--resume FILE]
 
@@ -81,6 +81,8 @@ def _anneal(argv):
     p.add_argument("--sweeps", type=int, default=None)
     p.add_argument("--beta", type=float, nargs=3, metavar=("LO", "HI", "K"), default=None)
     p.add_argument("--nlm-period", type=int, default=None)
+    p.add_argument("--nlm-kind", type=int, default=0, help="0 Houdayer pairs, 1 block moves")
+    p.add_argument("--nlm-block", type=int, default=32, help="block move size")
     p.add_argument("--field-bits", type=int, default=0)
     p.add_argument("--replicas-per-cta", type=int, default=0)
     p.add_argument("--threads", type=int, default=0)
@@ -117,7 +119,8 @@ def _anneal(argv):
             done = B.pa_run_info(ann.ctx)["steps_done"]
         else:
             ann.begin(betas, c["R"], c["S"], c["seed"], nlm_period=c["nlm_period"], field_bits=a.field_bits,
-                      replicas_per_cta=a.replicas_per_cta, threads_per_cta=a.threads, variant=a.variant)
+                      replicas_per_cta=a.replicas_per_cta, threads_per_cta=a.threads, variant=a.variant,
+                      nlm_kind=a.nlm_kind, nlm_block=a.nlm_block)
             done = 0
         every = a.checkpoint_every if a.checkpoint and a.checkpoint_every > 0 else max(K - done, 1)
         while done < K:
@@ -129,6 +132,8 @@ def _anneal(argv):
         dt = time.perf_counter() - t0
         st = ann.stats()
         cut, cfg, step, sweep = ann.best()
+        ss_all = ann.step_stats()
+        ss_nlm = (ss_all["nlm_pairs"].sum(), ss_all["nlm_flips"].sum())
         if a.curve:
             ss = ann.step_stats()
             W = st["total_weight"]
@@ -139,6 +144,7 @@ def _anneal(argv):
                     f.write(f"{k},{ss['beta'][k]:.17g},{ss['t_ms'][k]:.3f},{(W - int(best[k])) // 2}\n")
     out = dict(config=name, n=g.n, m=g.m, R=c["R"], S=c["S"], steps=K, seed=c["seed"], best_cut=cut,
                best_step=step, best_sweep=sweep, wall_s=dt, attempts=st["attempts"],
+               nlm_moves=int(ss_nlm[0]), nlm_flips=int(ss_nlm[1]),
                accepts=st["accepts"], device_ms=st["anneal_ms"],
                attempts_per_s=st["attempts"] / max(st["anneal_ms"], 1e-9) * 1e3)
     if a.hex or a.save_hex:

@@ -193,6 +193,132 @@ __global__ void k_nlm_pair(NlmArgs a, const int32_t *order) {
     }
 }
 
+// One CTA per slot. Warp 0 grows the block by breadth-first search (lanes
+// take a row's unvisited neighbours in row order through a ballot, so the
+// discovery order is the sequential one); the CTA then sums the edges that
+// leave the block, thread 0 decides, and an accepted move flips the block and
+// rebuilds the fields of the block and its neighbours.
+__global__ void __launch_bounds__(256) k_nlm_block(NlmArgs a) {
+    if (a.active && !a.active[a.k]) return;
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int np = a.g.np, n = a.g.n, nw = (np + 31) >> 5;
+    int8_t *x = reinterpret_cast<int8_t *>(sm);
+    uint32_t *inB = reinterpret_cast<uint32_t *>(x + np);   // np is a multiple of 16
+    uint32_t *aff = inB + nw;
+    int32_t *Bl = reinterpret_cast<int32_t *>(aff + nw);    // [block] positions in discovery order
+    __shared__ int sh_cnt, sh_acc;
+    __shared__ long long sh_red[8];
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
+    const int r = blockIdx.x;
+    {
+        const uint4 *gx = reinterpret_cast<const uint4 *>(a.spins + (size_t)r * np);
+        uint4 *lx = reinterpret_cast<uint4 *>(x);
+        for (int i = tid; i < (np >> 4); i += NT) lx[i] = gx[i];
+        for (int i = tid; i < nw; i += NT) {
+            inB[i] = 0u;
+            aff[i] = 0u;
+        }
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const uint4 us = philox10(make_uint4((uint32_t)r >> 2, 2u, (uint32_t)a.k, TAG_NONLOCAL), a.key0, a.key1);
+        const uint32_t uw[4] = {us.x, us.y, us.z, us.w};
+        const int ps = a.pos[uw[r & 3] % (uint32_t)n];
+        if (lane == 0) {
+            Bl[0] = ps;
+            inB[ps >> 5] = 1u << (ps & 31);
+        }
+        __syncwarp();
+        int cnt = 1, head = 0;   // warp-uniform
+        while (head < cnt && cnt < a.block) {
+            const int p = Bl[head++];
+            const uint32_t e1 = a.g.rp[p + 1];
+            for (uint32_t base = a.g.rp[p]; base < e1 && cnt < a.block; base += 32) {
+                const uint32_t e = base + lane;
+                int j = 0;
+                bool fresh = false;
+                if (e < e1) {
+                    j = a.g.col[e];
+                    fresh = !((inB[j >> 5] >> (j & 31)) & 1u);
+                }
+                const uint32_t mask = __ballot_sync(0xFFFFFFFFu, fresh);
+                const int take = min(__popc(mask), a.block - cnt);
+                const int rank = __popc(mask & ((1u << lane) - 1u));
+                if (fresh && rank < take) {
+                    Bl[cnt + rank] = j;
+                    atomicOr(&inB[j >> 5], 1u << (j & 31));
+                }
+                cnt += take;
+                __syncwarp();
+            }
+        }
+        if (lane == 0) sh_cnt = cnt;
+    }
+    __syncthreads();
+    const int cnt = sh_cnt;
+    // Sum of w x_i x_j over the edges leaving the block.
+    long long lv = 0;
+    for (int t = tid; t < cnt; t += NT) {
+        const int p = Bl[t];
+        const int xp = x[p];
+        const uint32_t e1 = a.g.rp[p + 1];
+        for (uint32_t e = a.g.rp[p]; e < e1; ++e) {
+            const int j = a.g.col[e];
+            if (!((inB[j >> 5] >> (j & 31)) & 1u)) lv += (long long)(a.g.wt ? (int)a.g.wt[e] : 1) * xp * x[j];
+        }
+    }
+    for (int off = 16; off; off >>= 1) lv += __shfl_xor_sync(0xFFFFFFFFu, lv, off);
+    if (lane == 0) sh_red[tid >> 5] = lv;
+    __syncthreads();
+    long long m = 0;
+    for (int w = 0; w < NT / 32; ++w) m -= sh_red[w];
+    if (tid == 0) {
+        int acc = m <= 0;
+        if (!acc) {
+            const uint4 ua = philox10(make_uint4((uint32_t)r >> 2, 3u, (uint32_t)a.k, TAG_NONLOCAL), a.key0, a.key1);
+            const uint32_t aw[4] = {ua.x, ua.y, ua.z, ua.w};
+            double pw = 1.0, sq = a.qrow[a.tidx[a.k]];
+            for (uint32_t d = (uint32_t)m; d; d >>= 1) {   // q^m: right-to-left square and multiply
+                if (d & 1u) pw = __dmul_rn(pw, sq);
+                sq = __dmul_rn(sq, sq);
+            }
+            const double v = floor(__dmul_rn(pw, 4294967296.0));
+            const uint32_t A = v >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)v;
+            acc = aw[r & 3] < A;
+        }
+        sh_acc = acc;
+    }
+    __syncthreads();
+    if (!sh_acc) return;
+    int8_t *gx = a.spins + (size_t)r * np;
+    for (int t = tid; t < cnt; t += NT) {
+        const int p = Bl[t];
+        const int8_t v = (int8_t)-x[p];
+        x[p] = v;
+        gx[p] = v;
+        atomicOr(&aff[p >> 5], 1u << (p & 31));
+        const uint32_t e1 = a.g.rp[p + 1];
+        for (uint32_t e = a.g.rp[p]; e < e1; ++e) {
+            const int j = a.g.col[e];
+            atomicOr(&aff[j >> 5], 1u << (j & 31));
+        }
+    }
+    __syncthreads();
+    int16_t *gh = a.fields + (size_t)r * np;
+    for (int p = tid; p < n; p += NT)
+        if ((aff[p >> 5] >> (p & 31)) & 1u) {
+            int h = 0;
+            const uint32_t e1 = a.g.rp[p + 1];
+            for (uint32_t e = a.g.rp[p]; e < e1; ++e) h += (a.g.wt ? (int)a.g.wt[e] : 1) * x[a.g.col[e]];
+            gh[p] = (int16_t)h;
+        }
+    if (tid == 0) {
+        a.E[r] += (int32_t)(2 * m);
+        atomicAdd(&a.pairs[a.k], 1);
+        atomicAdd(&a.flips[a.k], (unsigned long long)cnt);
+    }
+}
+
 // -------------------------------------------------------------- adaptive ---
 __global__ void k_ad_partials(AdaptArgs a) {
     const int n_prev = a.state[0];
@@ -284,6 +410,27 @@ __global__ void k_ad_choose(AdaptArgs a) {
         if (lane == 0) a.active[a.k] = 0;
         return;
     }
+    if (a.mode == 2) {
+        if (lane == 0) {
+            int j = a.state[1];
+            if (a.k > 0) {
+                const double acc = (double)a.accepts[a.k - 1];
+                if (acc < a.acc_lo_n) j = min(j + 1, a.J);
+                else if (acc > a.acc_hi_n) j = max(j - 1, 0);
+            }
+            int dn = 1 << (a.J - j);
+            if (dn > a.nmax - n_prev) dn = a.nmax - n_prev;
+            const int nk = n_prev + dn;
+            a.state[0] = nk;
+            a.state[1] = j;
+            a.qsel[a.k] = dn - 1;
+            a.tidx[a.k] = nk;
+            a.jsel[a.k] = j;
+            a.beta[a.k] = __dmul_rn((double)nk, a.delta);
+            a.active[a.k] = 1;
+        }
+        return;
+    }
     bool ok = false;
     if (lane <= a.J) {
         const double A = tree_sum_seq(a.part + ((size_t)lane * 2 + 0) * a.nch, a.nch);
@@ -306,7 +453,47 @@ __global__ void k_ad_choose(AdaptArgs a) {
     }
 }
 
+// ------------------------------------------------------------- reheating ---
+__global__ void k_rh_choose(ReheatArgs a) {
+    if (threadIdx.x != 0) return;
+    int i = 0, row = 0;
+    if (a.k > 0) {
+        const int ip = a.state[0];
+        int stall = a.state[1], best = a.state[2];
+        int step_min = 0x7FFFFFFF;
+        for (int s = 0; s < a.S; ++s) step_min = min(step_min, a.sweep_emin[(size_t)(a.k - 1) * a.S + s]);
+        if (step_min < best) {
+            best = step_min;
+            stall = 0;
+        } else {
+            ++stall;
+        }
+        if (stall >= a.after) {
+            i = max(0, ip - a.back);
+            stall = 0;
+        } else {
+            i = min(ip + 1, a.K - 1);
+        }
+        row = i == ip + 1 ? i : a.K;
+        a.state[1] = stall;
+        a.state[2] = best;
+    } else {
+        a.state[1] = 0;
+        a.state[2] = 0x7FFFFFFF;
+    }
+    a.state[0] = i;
+    a.tidx[a.k] = i;
+    a.qsel[a.k] = row;
+    a.isel[a.k] = i;
+    a.beta[a.k] = a.betas[i];
+}
+
 }  // namespace
+
+cudaError_t launch_reheat(const ReheatArgs &a, cudaStream_t st) {
+    k_rh_choose<<<1, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
 
 size_t nlm_scratch_bytes(int32_t R) { return (size_t)R * 8 + 256; }
 
@@ -314,7 +501,31 @@ size_t nlm_smem_bytes(int32_t np) {
     return (size_t)2 * np + 4 * (size_t)((np + 31) / 32) + 4 * (size_t)np + 16;
 }
 
+size_t nlm_block_smem_bytes(int32_t np, int32_t block) {
+    return (size_t)np + 8 * (size_t)((np + 31) / 32) + 4 * (size_t)block;
+}
+
 cudaError_t launch_nonlocal(const NlmArgs &a, void *scratch, cudaStream_t st, int *launches) {
+    if (a.kind == 1) {
+        *launches = 0;
+        if (a.R < 1) return cudaSuccess;
+        const size_t smem = nlm_block_smem_bytes(a.g.np, a.block);
+        static std::mutex mu;
+        static size_t raised = 48 * 1024;
+        {
+            std::lock_guard<std::mutex> lock(mu);
+            if (smem > raised) {   // per-function attribute: only ever raise it
+                cudaError_t e = cudaFuncSetAttribute(k_nlm_block, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+                raised = smem;
+            }
+        }
+        // Two warps per slot: the search is one warp's work, so small CTAs keep
+        // more searches in flight per SM.
+        k_nlm_block<<<a.R, 64, smem, st>>>(a);
+        *launches = 1;
+        return cudaGetLastError();
+    }
     uint32_t *keys = reinterpret_cast<uint32_t *>(scratch);
     int32_t *order = reinterpret_cast<int32_t *>(keys + a.R);
     const int nb = (a.R + 255) / 256;
@@ -340,7 +551,7 @@ cudaError_t launch_nonlocal(const NlmArgs &a, void *scratch, cudaStream_t st, in
 }
 
 cudaError_t launch_adapt(const AdaptArgs &a, cudaStream_t st) {
-    k_ad_partials<<<a.nch, RS_THREADS, 0, st>>>(a);
+    if (a.mode != 2) k_ad_partials<<<a.nch, RS_THREADS, 0, st>>>(a);
     k_ad_choose<<<1, 32, 0, st>>>(a);
     return cudaGetLastError();
 }

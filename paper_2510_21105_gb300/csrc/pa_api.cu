@@ -99,17 +99,19 @@ struct RunState {
     std::vector<double> betas;           // per step (fixed schedule)
     std::vector<uint32_t> tables;        // [ntables][mmax+1]
     std::vector<double> qpow;            // [nq][32]
+    std::vector<double> qblk;            // [ntables] exp(-2 beta) of each table row (block moves)
     int32_t ntables = 0, nq = 0;
     // device
     DevBuf spins[2], fields[2], E[2], parent;
     DevBuf partA, partT, tval, ploc;
-    DevBuf d_tables, d_tidx, d_qpow;
+    DevBuf d_tables, d_tidx, d_qpow, d_qblk;
     DevBuf rec_emin, rec_A, rec_T, rec_o, rec_acc, rec_sweep, rec_stamp, rec_counts;
     DevBuf rec_nlm_pairs, rec_nlm_flips, rec_jsel;
     DevBuf best_rec, best_cfg;
     DevBuf nlm_scratch;
     // adaptive
     DevBuf ad_state, ad_qsel, ad_active, ad_beta, ad_part;
+    DevBuf d_betas;                      // reheating: the schedule on the device
     double ad_delta = 0.0;
     int32_t ad_nmax = 0;
     int cur = 0;
@@ -248,11 +250,20 @@ int validate_opts(pa_ctx *c, const pa_anneal_opts &o) {
     if (o.variant == PA_VARIANT_MSC && o.threads_per_cta > 256)
         return fail(c, PA_EINVAL, "the multi-spin-coded variant runs at most 256 threads per CTA");
     if (o.nlm_period < 0) return fail(c, PA_EINVAL, "nlm_period < 0");
+    if (o.nlm_kind != 0 && o.nlm_kind != 1) return fail(c, PA_EINVAL, "nlm_kind must be 0 or 1");
+    if (o.nlm_kind == 1 && (o.nlm_block < 1 || o.nlm_block > 1024))
+        return fail(c, PA_EINVAL, "nlm_block must be 1..1024");
     if (o.replicas_per_cta != 0 && o.replicas_per_cta != 4 && o.replicas_per_cta != 8)
         return fail(c, PA_EINVAL, "replicas_per_cta must be 0, 4 or 8");
     if (o.threads_per_cta != 0 &&
         (o.threads_per_cta < 128 || o.threads_per_cta > 1024 || o.threads_per_cta % 32))
         return fail(c, PA_EINVAL, "threads_per_cta");
+    if (o.adaptive < 0 || o.adaptive > 2) return fail(c, PA_EINVAL, "adaptive must be 0, 1 or 2");
+    if (o.adaptive == 2 && !(o.acc_lo >= 0.0 && o.acc_lo <= o.acc_hi && o.acc_hi <= 1.0))
+        return fail(c, PA_EINVAL, "acceptance band needs 0 <= acc_lo <= acc_hi <= 1");
+    if (o.reheat_after < 0) return fail(c, PA_EINVAL, "reheat_after < 0");
+    if (o.reheat_after > 0 && o.adaptive) return fail(c, PA_EINVAL, "reheating needs a fixed schedule");
+    if (o.reheat_after > 0 && o.reheat_back < 1) return fail(c, PA_EINVAL, "reheat_back must be >= 1");
     if (o.adaptive) {
         if (!(o.rho > 0.0 && o.rho <= 1.0)) return fail(c, PA_EINVAL, "rho must be in (0, 1]");
         if (o.adapt_J < 0 || o.adapt_J > 20) return fail(c, PA_EINVAL, "adapt_J must be 0..20");
@@ -298,6 +309,9 @@ void pa_default_opts(pa_anneal_opts *o) {
     o->rho = 0.5;
     o->adapt_J = 8;
     o->adapt_dbeta_max = 0.05;
+    o->nlm_block = 32;
+    o->acc_lo = 0.05;
+    o->acc_hi = 0.25;
 }
 
 int pa_create(pa_ctx **out, int32_t n, const uint32_t *row_ptr, const uint16_t *col, const int8_t *w) {
@@ -482,7 +496,7 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     if (K < 0 || R < 1 || R > 65536 || sweeps < 0 || sweeps >= (1 << 28))
         return fail(c, PA_EINVAL, "K, R (1..65536) or sweeps out of range");
     if (int rc = validate_opts(c, o)) return rc;
-    if (o.nlm_period > 0 && pa::nlm_smem_bytes(c->np) > 200 * 1024)
+    if (o.nlm_period > 0 && o.nlm_kind == 0 && pa::nlm_smem_bytes(c->np) > 200 * 1024)
         return fail(c, PA_EINVAL, "non-local moves support n <= 32768");
     if (!o.adaptive) {
         if (K > 0 && !betas) return fail(c, PA_EINVAL, "betas is NULL");
@@ -523,7 +537,8 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
         r.betas.assign(betas, betas + K);
         r.ntables = std::max(K, 1);
         r.tables.assign((size_t)r.ntables * (mmax + 1), 0u);
-        r.nq = std::max(K, 1);
+        // Reheating adds row K: q = 1 for steps that do not advance the schedule.
+        r.nq = std::max(K, 1) + (o.reheat_after > 0 ? 1 : 0);
         r.qpow.assign((size_t)r.nq * 32, 0.0);
         double prev = 0.0;
         for (int32_t k = 0; k < K; ++k) {
@@ -531,6 +546,7 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
             qpow_row(std::exp(-(betas[k] - prev)), &r.qpow[(size_t)k * 32]);
             prev = betas[k];
         }
+        if (o.reheat_after > 0) qpow_row(1.0, &r.qpow[(size_t)(r.nq - 1) * 32]);
     } else {
         r.betas.clear();
         r.ad_delta = std::ldexp(o.adapt_dbeta_max, -o.adapt_J);
@@ -545,6 +561,15 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
         r.qpow.assign((size_t)r.nq * 32, 0.0);
         for (int32_t dn = 1; dn <= r.nq; ++dn)
             qpow_row(std::exp(-((double)dn * r.ad_delta)), &r.qpow[(size_t)(dn - 1) * 32]);
+    }
+    // Block moves: q = exp(-2 beta) of every table row (beta_k, or n delta when adaptive).
+    r.qblk.clear();
+    if (o.nlm_period > 0 && o.nlm_kind == 1) {
+        r.qblk.assign((size_t)r.ntables, 1.0);
+        for (int32_t t = 0; t < r.ntables; ++t) {
+            const double beta = o.adaptive ? (double)t * r.ad_delta : (t < K ? betas[t] : 0.0);
+            r.qblk[t] = std::exp(-2.0 * beta);
+        }
     }
     // Device buffers (stream-ordered on the context's stream).
     cudaStream_t ST = c->stream();
@@ -569,11 +594,17 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     if (ok && o.adaptive)
         ok = r.ad_state.alloc(16, ST) && r.ad_qsel.alloc(4 * (size_t)Kc, ST) && r.ad_active.alloc(4 * (size_t)Kc, ST) &&
              r.ad_beta.alloc(8 * (size_t)Kc, ST) && r.ad_part.alloc(16 * (size_t)(o.adapt_J + 1) * r.nch, ST);
+    if (ok && o.reheat_after > 0)
+        ok = r.ad_state.alloc(16, ST) && r.ad_qsel.alloc(4 * (size_t)Kc, ST) && r.ad_beta.alloc(8 * (size_t)Kc, ST) &&
+             r.d_betas.alloc(8 * (size_t)Kc, ST);
     if (ok && o.nlm_period > 0) ok = r.nlm_scratch.alloc(pa::nlm_scratch_bytes(R), ST);
+    if (ok && !r.qblk.empty()) ok = r.d_qblk.alloc(8 * r.qblk.size(), ST);
     if (!ok) return fail(c, PA_ENOMEM, "device allocation failed");
     cudaStream_t st = c->stream();
     PA_CUDA(c, copy(c, r.d_tables.p, r.tables.data(), 4 * r.tables.size(), cudaMemcpyHostToDevice, st, true));
     PA_CUDA(c, copy(c, r.d_qpow.p, r.qpow.data(), 8 * r.qpow.size(), cudaMemcpyHostToDevice, st, true));
+    if (!r.qblk.empty())
+        PA_CUDA(c, copy(c, r.d_qblk.p, r.qblk.data(), 8 * r.qblk.size(), cudaMemcpyHostToDevice, st, true));
     {
         std::vector<int32_t> tidx(Kc);
         for (int32_t k = 0; k < Kc; ++k) tidx[k] = o.adaptive ? 0 : k;
@@ -598,6 +629,12 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     PA_CUDA(c, cudaMemsetAsync(r.rec_jsel.p, 0xFF, 4 * (size_t)Kc, st));
     PA_CUDA(c, cudaMemsetAsync(r.best_cfg.p, 0, (size_t)r.nblk * c->np, st));
     if (o.record_counts) PA_CUDA(c, cudaMemsetAsync(r.rec_counts.p, 0, 4 * (size_t)Kc * R, st));
+    if (o.reheat_after > 0) {
+        PA_CUDA(c, cudaMemsetAsync(r.ad_state.p, 0, 16, st));
+        PA_CUDA(c, cudaMemsetAsync(r.ad_qsel.p, 0, 4 * (size_t)Kc, st));
+        PA_CUDA(c, cudaMemsetAsync(r.ad_beta.p, 0, 8 * (size_t)Kc, st));
+        if (K > 0) PA_CUDA(c, copy(c, r.d_betas.p, r.betas.data(), 8 * (size_t)K, cudaMemcpyHostToDevice, st, true));
+    }
     if (o.adaptive) {
         PA_CUDA(c, cudaMemsetAsync(r.ad_state.p, 0, 16, st));
         PA_CUDA(c, cudaMemsetAsync(r.ad_active.p, 0, 4 * (size_t)Kc, st));
@@ -634,7 +671,24 @@ int enqueue_step(pa_ctx *c, int32_t k, cudaStream_t st, bool time_sweep) {
     ra.key0 = k0;
     ra.key1 = k1;
     ra.qpow = r.d_qpow.as<double>();
-    ra.qsel = o.adaptive ? r.ad_qsel.as<int32_t>() : nullptr;
+    ra.qsel = (o.adaptive || o.reheat_after > 0) ? r.ad_qsel.as<int32_t>() : nullptr;
+    if (o.reheat_after > 0) {
+        pa::ReheatArgs ha{};
+        ha.sweep_emin = r.rec_sweep.as<int32_t>();
+        ha.betas = r.d_betas.as<double>();
+        ha.k = k;
+        ha.K = r.K;
+        ha.S = r.S;
+        ha.after = o.reheat_after;
+        ha.back = o.reheat_back;
+        ha.state = r.ad_state.as<int32_t>();
+        ha.tidx = r.d_tidx.as<int32_t>();
+        ha.qsel = r.ad_qsel.as<int32_t>();
+        ha.isel = r.rec_jsel.as<int32_t>();
+        ha.beta = r.ad_beta.as<double>();
+        PA_CUDA(c, pa::launch_reheat(ha, st));
+        r.launches += 1;
+    }
     ra.active = nullptr;   // the minimum runs before the adaptive decision
     ra.emin = r.rec_emin.as<int32_t>();
     ra.partA = r.partA.as<double>();
@@ -668,8 +722,13 @@ int enqueue_step(pa_ctx *c, int32_t k, cudaStream_t st, bool time_sweep) {
         aa.tidx = r.d_tidx.as<int32_t>();
         aa.jsel = r.rec_jsel.as<int32_t>();
         aa.beta = r.ad_beta.as<double>();
+        aa.mode = o.adaptive;
+        aa.accepts = r.rec_acc.as<unsigned long long>();
+        const double attempts = (double)((int64_t)c->n * r.R * r.S);
+        aa.acc_lo_n = o.acc_lo * attempts;
+        aa.acc_hi_n = o.acc_hi * attempts;
         PA_CUDA(c, pa::launch_adapt(aa, st));
-        r.launches += 2;
+        r.launches += o.adaptive == 2 ? 1 : 2;
         ra.active = r.ad_active.as<int32_t>();
     }
     PA_CUDA(c, pa::launch_rs_rest(ra, st));
@@ -724,6 +783,10 @@ int enqueue_step(pa_ctx *c, int32_t k, cudaStream_t st, bool time_sweep) {
         na.active = o.adaptive ? r.ad_active.as<int32_t>() : nullptr;
         na.pairs = r.rec_nlm_pairs.as<int32_t>();
         na.flips = r.rec_nlm_flips.as<unsigned long long>();
+        na.kind = o.nlm_kind;
+        na.block = o.nlm_block;
+        na.qrow = r.d_qblk.as<double>();
+        na.tidx = r.d_tidx.as<int32_t>();
         int nl = 0;
         PA_CUDA(c, pa::launch_nonlocal(na, r.nlm_scratch.p, st, &nl));
         r.launches += nl;
@@ -1076,7 +1139,7 @@ int pa_step_stats(pa_ctx *c, pa_step_arrays *out) {
     PA_CUDA(c, copy(c, emin.data(), r.rec_emin.p, 4 * (size_t)ks, cudaMemcpyDeviceToHost));
     PA_CUDA(c, copy(c, A.data(), r.rec_A.p, 8 * (size_t)ks, cudaMemcpyDeviceToHost));
     std::vector<double> beta(ks);
-    if (r.opts.adaptive)
+    if (r.opts.adaptive || r.opts.reheat_after > 0)
         PA_CUDA(c, copy(c, beta.data(), r.ad_beta.p, 8 * (size_t)ks, cudaMemcpyDeviceToHost));
     else
         for (int32_t k = 0; k < ks; ++k) beta[k] = r.betas[k];
@@ -1164,6 +1227,12 @@ std::vector<RecSpec> ckpt_records(RunState &r) {
         v.push_back({&r.ad_state, 0, 16});
         v.push_back({&r.ad_qsel, 4, 0});
         v.push_back({&r.ad_active, 4, 0});
+        v.push_back({&r.ad_beta, 8, 0});
+        v.push_back({&r.d_tidx, 4, 0});
+    }
+    if (r.opts.reheat_after > 0) {
+        v.push_back({&r.ad_state, 0, 16});
+        v.push_back({&r.ad_qsel, 4, 0});
         v.push_back({&r.ad_beta, 8, 0});
         v.push_back({&r.d_tidx, 4, 0});
     }

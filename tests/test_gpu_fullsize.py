@@ -19,8 +19,10 @@ def _gpu():
     require_gpu()
 
 
-def _replay_check(g, betas, R, S, seed, k, subset, nlm_period=0, **opts):
+def _replay_check(g, betas, R, S, seed, k, subset, nlm_period=0, nlm_block=0, **opts):
     a = B.Annealer.from_graph(g)
+    if nlm_block:
+        opts.update(nlm_kind=1, nlm_block=nlm_block)
     a.begin(betas, R, S, seed, record_counts=1, nlm_period=nlm_period, **opts)
     a.run(k)
     a.sync()
@@ -32,7 +34,7 @@ def _replay_check(g, betas, R, S, seed, k, subset, nlm_period=0, **opts):
     a.close()
     nlm_now = nlm_period > 0 and k > 0 and k % nlm_period == 0
     rep = oracle.step_replay(g.rp, g.col, g.w, spins_a, S, seed, k, betas[k - 1] if k else 0.0,
-                             betas[k], subset, nlm_now=nlm_now)
+                             betas[k], subset, nlm_now=nlm_now, nlm_block=nlm_block)
     np.testing.assert_array_equal(counts, rep["counts"], err_msg="copy counts at full size")
     assert counts.sum() == R
     np.testing.assert_array_equal(spins_b[subset], rep["spins"], err_msg="replayed spins")
@@ -59,6 +61,17 @@ def test_replay_g63like_nonlocal_step():
     order = oracle.nlm_order(c["R"], c["seed"], k)
     subset = np.array(sorted(order[[0, 1, 2000, 2001, 16382, 16383]].tolist()))
     _replay_check(g, betas, c["R"], c["S"], c["seed"], k, subset, nlm_period=k)
+
+
+def test_replay_g63like_block_move_step():
+    """Block moves (b = 32) at the first non-local step of the full workload,
+    in the launch configuration of the benchmark (multi-spin-coded sweeps)."""
+    c = wl.CONFIGS["g63like"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    k = c["nlm_period"]
+    subset = np.array([0, 1, 2, 3, 777, 4096, 9999, 16383])
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], k, subset, nlm_period=k, nlm_block=32)
 
 
 @pytest.mark.parametrize("variant", [0, 1])

@@ -96,6 +96,72 @@ def test_parity_nonlocal_moves(variant):
     assert_parity(gpu, orc, g, 64, 3)
 
 
+@pytest.mark.parametrize("block", [1, 13, 300])
+@pytest.mark.parametrize("variant,field_bits", [(0, 16), (0, 7), (1, 0)], ids=["int16", "packed", "msc"])
+def test_parity_block_moves(variant, field_bits, block):
+    """Block moves (nlm_kind = 1) on a signed graph in every layout: b = 1 is
+    a single Metropolis flip, b = 300 covers the seed's whole component."""
+    g = wl.from_edges(300, *_random_edges(300, 900, seed=55))
+    betas = wl.linear_betas(0.02, 1.2, 10)
+    kw = dict(nlm_period=2, nlm_kind=1, nlm_block=block)
+    gpu = run_gpu(g, betas, 50, 2, seed=23, variant=variant, field_bits=field_bits, **kw)
+    orc = run_oracle(g, betas, 50, 2, seed=23, **kw)
+    assert orc.step_nlm_pairs.sum() > 0
+    assert_parity(gpu, orc, g, 50, 2)
+
+
+def test_parity_block_moves_adaptive():
+    g = wl.gnp(150, 0.06, seed=56)
+    kw = dict(adaptive=1, rho=0.6, adapt_J=4, adapt_dbeta_max=0.2, beta_max=1.0, nlm_period=2, nlm_kind=1,
+              nlm_block=9)
+    gpu = run_gpu(g, None, 64, 2, seed=29, K=200, **kw)
+    orc = run_oracle(g, None, 64, 2, seed=29, K=200, **{**kw, "adaptive": True})
+    assert orc.step_nlm_pairs.sum() > 0
+    np.testing.assert_array_equal(gpu["rec"]["jsel"], orc.step_jsel)
+    assert_parity(gpu, orc, g, 64, 2)
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_parity_acceptance_rate_control(variant):
+    """adaptive = 2 (acceptance-rate rule), alone and with block moves."""
+    g = wl.from_edges(250, *_random_edges(250, 1000, seed=58))
+    kw = dict(adaptive=2, adapt_J=4, adapt_dbeta_max=0.4, beta_max=3.0, acc_lo=0.12, acc_hi=0.3)
+    for extra in (dict(), dict(nlm_period=1, nlm_kind=1, nlm_block=2)):
+        gpu = run_gpu(g, None, 72, 2, seed=37, K=400, variant=variant, **kw, **extra)
+        orc = run_oracle(g, None, 72, 2, seed=37, K=400, **kw, **extra)
+        assert 0 < orc.steps_run < 400 and len(set(orc.step_jsel.tolist())) >= 3
+        np.testing.assert_array_equal(gpu["rec"]["jsel"], orc.step_jsel)
+        assert_parity(gpu, orc, g, 72, 2)
+
+
+@pytest.mark.parametrize("variant,field_bits", [(0, 16), (0, 7), (1, 0)], ids=["int16", "packed", "msc"])
+def test_parity_stagnation_reheating(variant, field_bits):
+    """Stagnation reheating on a fixed schedule, alone and with block moves;
+    the schedule index of every step is compared."""
+    g = wl.gnm(150, 600, seed=47)
+    betas = wl.linear_betas(0.1, 3.0, 60)
+    for extra in (dict(), dict(nlm_period=4, nlm_kind=1, nlm_block=3)):
+        kw = dict(reheat_after=3, reheat_back=10, **extra)
+        gpu = run_gpu(g, betas, 40, 2, seed=4, variant=variant, field_bits=field_bits, **kw)
+        orc = run_oracle(g, betas, 40, 2, seed=4, **kw)
+        assert len(set(np.diff(orc.step_jsel).tolist())) >= 2      # at least one reheat
+        np.testing.assert_array_equal(gpu["rec"]["jsel"], orc.step_jsel)
+        assert_parity(gpu, orc, g, 40, 2)
+
+
+def test_block_move_options_are_validated():
+    g = wl.gnp(50, 0.1, seed=57)
+    a = B.Annealer.from_graph(g)
+    for kw in (dict(nlm_kind=2), dict(nlm_kind=1, nlm_block=0), dict(nlm_kind=1, nlm_block=1025),
+               dict(adaptive=3), dict(adaptive=2, acc_lo=0.5, acc_hi=0.4), dict(adaptive=2, acc_hi=1.5),
+               dict(reheat_after=-1), dict(reheat_after=2, reheat_back=0),
+               dict(reheat_after=2, reheat_back=1, adaptive=1, beta_max=1.0)):
+        with pytest.raises(B.PaError) as e:
+            a.begin(wl.linear_betas(0.1, 1.0, 3), R=8, S=1, seed=1, nlm_period=1, **kw)
+        assert e.value.code == B.PA_EINVAL
+    a.close()
+
+
 def test_parity_adaptive_steps():
     g = wl.gnp(120, 0.08, seed=13)
     kw = dict(adaptive=1, rho=0.6, adapt_J=5, adapt_dbeta_max=0.25, beta_max=2.0)
@@ -135,7 +201,8 @@ def test_degenerate_cases():
     (dict(nlm_period=4), 10, 6),
     (dict(variant=1), 10, 3),
     (dict(adaptive=1, rho=0.5, adapt_J=4, adapt_dbeta_max=0.3, beta_max=1.5, nlm_period=3), 40, 7),
-], ids=["fixed-nlm", "msc", "adaptive"])
+    (dict(reheat_after=2, reheat_back=3, nlm_period=2, nlm_kind=1, nlm_block=4), 24, 11),
+], ids=["fixed-nlm", "msc", "adaptive", "reheat-block"])
 def test_checkpoint_resume_is_bit_exact(tmp_path, kw, K, split):
     """A run saved after `split` steps and resumed in a fresh context equals
     the uninterrupted run: population, best record and every per-step record

@@ -280,6 +280,96 @@ def test_houdayer_cluster_is_connected_component_and_conserves_energy():
             assert np.array_equal(ya[~cl], xa[~cl]) and np.array_equal(yb[~cl], xb[~cl])
 
 
+def _edge_energy(g, x):
+    """E = sum over undirected edges of w x_i x_j, from the edge list."""
+    i, j, w = g.edges()
+    return int(np.sum(w.astype(np.int64) * x[i] * x[j]))
+
+
+def test_block_move_block_is_bfs_prefix_and_energy_change_is_exact():
+    nx = pytest.importorskip("networkx")
+    rng = np.random.default_rng(5)
+    for g in [wl.gnp(90, 0.06, seed=41), wl.torus(9, seed=42), wl.gnm(200, 500, seed=43)]:
+        i, j, _ = g.edges()
+        G = nx.Graph()
+        G.add_nodes_from(range(g.n))
+        G.add_edges_from(zip(i.tolist(), j.tolist()))
+        for trial in range(25):
+            x = rng.choice(np.array([-1, 1], np.int8), size=g.n)
+            E = _edge_energy(g, x)
+            b = int(rng.integers(1, 40))
+            sv = int(rng.integers(0, g.n))
+            order = [sv] + [v for _, v in nx.bfs_edges(G, sv, sort_neighbors=sorted)]
+            want = set(order[:b])
+            size, y, E2, mask = oracle.block_move(g.rp, g.col, g.w, x, E, b, 1.0, sv, 0)
+            assert set(np.flatnonzero(mask).tolist()) == want
+            # q = 1 (beta = 0): every move is accepted
+            assert size == len(want)
+            flipped = x.copy()
+            flipped[list(want)] *= -1
+            assert np.array_equal(y, flipped)
+            assert E2 == _edge_energy(g, flipped)
+
+
+def test_block_move_acceptance_threshold_is_boltzmann_factor():
+    mp = pytest.importorskip("mpmath")
+    g = wl.gnm(120, 400, seed=44)
+    rng = np.random.default_rng(6)
+    checked = 0
+    for trial in range(200):
+        x = rng.choice(np.array([-1, 1], np.int8), size=g.n)
+        E = _edge_energy(g, x)
+        sv, b = int(rng.integers(0, g.n)), int(rng.integers(1, 12))
+        _, y, E1, mask = oracle.block_move(g.rp, g.col, g.w, x, E, b, 1.0, sv, 0)
+        m = (E1 - E) // 2
+        beta = float(rng.uniform(0.05, 1.0))
+        q = math.exp(-2.0 * beta)
+        if m <= 0:
+            size, *_ = oracle.block_move(g.rp, g.col, g.w, x, E, b, q, sv, 2**32 - 1)
+            assert size == int(mask.sum())
+            continue
+        exact = int(mp.floor(mp.ldexp(mp.exp(-2 * mp.mpf(beta) * m), 32)))
+        if exact < 4:
+            continue
+        acc_lo, *_ = oracle.block_move(g.rp, g.col, g.w, x, E, b, q, sv, exact - 2)
+        acc_hi, *_ = oracle.block_move(g.rp, g.col, g.w, x, E, b, q, sv, exact + 1)
+        assert acc_lo == int(mask.sum()) and acc_hi == 0
+        checked += 1
+    assert checked > 20
+
+
+def test_block_move_of_one_spin_is_a_metropolis_flip():
+    g = wl.gnp(60, 0.1, seed=45)
+    rng = np.random.default_rng(7)
+    beta = 0.7
+    T = oracle.accept_table(beta, g.maxdeg)
+    for trial in range(60):
+        x = rng.choice(np.array([-1, 1], np.int8), size=g.n)
+        E = _edge_energy(g, x)
+        v = int(rng.integers(0, g.n))
+        row = g.col[g.rp[v]:g.rp[v + 1]]
+        m = int(-x[v] * x[row].sum())          # unweighted: h_v = sum of neighbour spins
+        u = int(rng.integers(0, 2**32))
+        size, y, E2, _ = oracle.block_move(g.rp, g.col, g.w, x, E, 1, math.exp(-2.0 * beta), v, u)
+        if m <= 0:
+            assert size == 1 and E2 == E + 2 * m
+        elif abs(int(u) - int(T[m])) > 2:      # away from the rounding of the threshold
+            assert (size == 1) == (u < int(T[m]))
+
+
+def test_block_move_covers_whole_component_when_b_is_large():
+    nx = pytest.importorskip("networkx")
+    g = wl.from_edges(10, [0, 1, 2, 5, 6], [1, 2, 3, 6, 7])
+    i, j, _ = g.edges()
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    G.add_edges_from(zip(i.tolist(), j.tolist()))
+    x = np.ones(g.n, np.int8)
+    size, y, E2, mask = oracle.block_move(g.rp, g.col, g.w, x, _edge_energy(g, x), 100, 1.0, 2, 0)
+    assert set(np.flatnonzero(mask).tolist()) == nx.node_connected_component(G, 2) == {0, 1, 2, 3}
+    assert size == 4 and E2 == _edge_energy(g, y)
+
+
 def test_nlm_pairing_is_a_permutation():
     order = oracle.nlm_order(1000, 42, 50)
     assert sorted(order.tolist()) == list(range(1000))
@@ -345,3 +435,85 @@ def test_hex_roundtrip_odd_lengths():
     for n in [1, 3, 4, 5, 17, 801]:
         x = rng.choice(np.array([-1, 1], np.int8), size=n)
         assert np.array_equal(hexconfig.decode(hexconfig.encode(x), n), x)
+
+
+def test_anneal_with_block_moves_keeps_energies_exact():
+    """Whole anneals with block moves: carried energies equal recomputation,
+    every move is counted, and b = 1 moves flip one spin each."""
+    g = wl.torus(10, seed=46)
+    betas = wl.linear_betas(0.02, 0.3, 12)     # hot enough for blocks of 40 to be accepted
+    for b in (1, 7, 40):
+        res = oracle.anneal(g.rp, g.col, g.w, betas, R=24, S=1, seed=9, nlm_period=3, nlm_kind=1, nlm_block=b)
+        for r in range(24):
+            assert res.E[r] == _edge_energy(g, res.spins[r])
+        due = [k for k in range(12) if k > 0 and k % 3 == 0]
+        assert np.all(res.step_nlm_pairs[[k for k in range(12) if k not in due]] == 0)
+        assert res.step_nlm_pairs[due].sum() > 0
+        assert np.all(res.step_nlm_flips <= b * res.step_nlm_pairs)
+        if b == 1:
+            assert np.array_equal(res.step_nlm_flips, res.step_nlm_pairs)
+
+
+def test_acceptance_rate_control_follows_recorded_rates():
+    """adaptive = 2: the level sequence recomputed from the recorded accepted
+    flips (which the sweeps pins above fix), and beta advances by the grid
+    step of each level, monotonically, to beta_max."""
+    g = wl.gnm(150, 600, seed=47)
+    R, S, J, dmax, bmax, lo, hi = 40, 2, 4, 0.4, 3.0, 0.12, 0.3
+    res = oracle.anneal(g.rp, g.col, g.w, None, R=R, S=S, seed=3, K=400, adaptive=2, adapt_J=J,
+                        adapt_dbeta_max=dmax, beta_max=bmax, acc_lo=lo, acc_hi=hi)
+    K = res.steps_run
+    assert 0 < K < 400
+    delta = math.ldexp(dmax, -J)
+    nmax = int(math.floor(bmax / delta + 0.5))
+    attempts = g.n * R * S
+    j, n_prev = 0, 0
+    seen = set()
+    for k in range(K):
+        if k > 0:
+            rate = res.step_accepts[k - 1]
+            if rate < lo * attempts:
+                j = min(j + 1, J)
+            elif rate > hi * attempts:
+                j = max(j - 1, 0)
+        seen.add(j)
+        assert res.step_jsel[k] == j
+        n_prev += min(2 ** (J - j), nmax - n_prev)
+        assert res.step_beta[k] == n_prev * delta
+    assert res.step_beta[-1] == pytest.approx(bmax)
+    assert len(seen) >= 3                      # the band moves the level both ways
+    assert np.all(np.diff(res.step_beta) > 0)
+
+
+def test_stagnation_reheating_follows_recorded_minima():
+    """reheat_after > 0: the schedule index sequence recomputed from the
+    recorded sweep minima; steps that do not advance the index resample with
+    q = 1, which is the identity (every copy count 1, A = R)."""
+    g = wl.gnm(150, 600, seed=47)
+    betas = wl.linear_betas(0.1, 3.0, 60)
+    R, S, Q, back = 32, 2, 3, 10
+    res = oracle.anneal(g.rp, g.col, g.w, betas, R=R, S=S, seed=4, reheat_after=Q, reheat_back=back,
+                        record_counts=True)
+    i_prev, stall, best = 0, 0, 2**31 - 1
+    reheats = 0
+    for k in range(60):
+        i = 0
+        if k > 0:
+            m = int(res.step_sweep_emin[k - 1].min())
+            if m < best:
+                best, stall = m, 0
+            else:
+                stall += 1
+            if stall >= Q:
+                i, stall = max(0, i_prev - back), 0
+                reheats += 1
+            else:
+                i = min(i_prev + 1, 59)
+        assert res.step_jsel[k] == i
+        assert res.step_beta[k] == betas[i]
+        if k > 0 and i != i_prev + 1:
+            assert np.all(res.step_counts[k] == 1) and res.step_A[k] == R
+        i_prev = i
+    assert reheats >= 2
+    plain = oracle.anneal(g.rp, g.col, g.w, betas, R=R, S=S, seed=4)
+    assert not np.array_equal(plain.step_beta, res.step_beta)
