@@ -568,14 +568,14 @@ struct PhiloxShared {
 __device__ __forceinline__ PhiloxShared philox_shared(uint32_t c0, uint32_t c2, uint32_t c3, uint32_t k0,
                                                       uint32_t k1) {
     PhiloxShared p;
-    p.u1 = __umulhi(0xCD9E8D57u, c2) ^ k0;
-    p.l1 = 0xCD9E8D57u * c2;
-    p.a = __umulhi(0xD2511F53u, c0) ^ c3 ^ k1;
-    p.b = 0xD2511F53u * c0;
-    p.s0 = __umulhi(0xCD9E8D57u, p.a) ^ p.l1 ^ (k0 + 0x9E3779B9u);
-    p.s1 = 0xCD9E8D57u * p.a;
-    p.h3 = __umulhi(0xD2511F53u, p.s0);
-    p.l3 = 0xD2511F53u * p.s0;
+    uint32_t hi;
+    mul_wide(0xCD9E8D57u, c2, p.l1, hi);
+    p.u1 = hi ^ k0;
+    mul_wide(0xD2511F53u, c0, p.b, hi);
+    p.a = hi ^ c3 ^ k1;
+    mul_wide(0xCD9E8D57u, p.a, p.s1, hi);
+    p.s0 = hi ^ p.l1 ^ (k0 + 0x9E3779B9u);
+    mul_wide(0xD2511F53u, p.s0, p.l3, p.h3);
     return p;
 }
 
@@ -583,17 +583,21 @@ __device__ __forceinline__ uint4 philox_from_shared(const PhiloxShared &p, uint3
     // round 1 (only word 0 depends on c1)
     const uint32_t n0 = p.u1 ^ c1;
     // round 2: word 2 product shared (s0, s1); word 0 product per counter
-    uint4 c = make_uint4(p.s0, p.s1, __umulhi(0xD2511F53u, n0) ^ p.b ^ (k1 + 0xBB67AE85u), 0xD2511F53u * n0);
+    uint32_t lo, hi;
+    mul_wide(0xD2511F53u, n0, lo, hi);
+    uint4 c = make_uint4(p.s0, p.s1, hi ^ p.b ^ (k1 + 0xBB67AE85u), lo);
     // round 3: word 0 product shared (h3, l3)
     k0 += 2u * 0x9E3779B9u;
     k1 += 2u * 0xBB67AE85u;
-    c = make_uint4(__umulhi(0xCD9E8D57u, c.z) ^ c.y ^ k0, 0xCD9E8D57u * c.z, p.h3 ^ c.w ^ k1, p.l3);
+    mul_wide(0xCD9E8D57u, c.z, lo, hi);
+    c = make_uint4(hi ^ c.y ^ k0, lo, p.h3 ^ c.w ^ k1, p.l3);
 #pragma unroll
     for (int r = 3; r < 10; ++r) {
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), hi1 = __umulhi(0xCD9E8D57u, c.z);
-        const uint32_t lo0 = 0xD2511F53u * c.x, lo1 = 0xCD9E8D57u * c.z;
+        uint32_t lo0, hi0, lo1, hi1;
+        mul_wide(0xD2511F53u, c.x, lo0, hi0);
+        mul_wide(0xCD9E8D57u, c.z, lo1, hi1);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
     }
     return c;

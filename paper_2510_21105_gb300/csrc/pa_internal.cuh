@@ -15,21 +15,27 @@
 
 namespace pa {
 
+// Full 32x32 -> 64-bit product (both halves from one wide multiply).
+__host__ __device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32_t &lo, uint32_t &hi) {
+#ifdef __CUDA_ARCH__
+    unsigned long long p;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(p) : "r"(a), "r"(b));
+#else
+    const uint64_t p = (uint64_t)a * b;
+#endif
+    lo = (uint32_t)p;
+    hi = (uint32_t)(p >> 32);
+}
+
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
 // multiplies by 0xD2511F53 / 0xCD9E8D57, high halves xored with the other
 // counter words and the key; key advanced by 0x9E3779B9 / 0xBB67AE85.
 __host__ __device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-#ifdef __CUDA_ARCH__
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-#else
-        const uint32_t hi0 = (uint32_t)(((uint64_t)0xD2511F53u * c.x) >> 32);
-        const uint32_t hi1 = (uint32_t)(((uint64_t)0xCD9E8D57u * c.z) >> 32);
-#endif
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        uint32_t lo0, hi0, lo1, hi1;
+        mul_wide(0xD2511F53u, c.x, lo0, hi0);
+        mul_wide(0xCD9E8D57u, c.z, lo1, hi1);
         c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
         k0 += 0x9E3779B9u;
         k1 += 0xBB67AE85u;
