@@ -46,6 +46,7 @@ def parse():
     p.add_argument("--mode", default="anneal", choices=["anneal", "batch", "serve"],
                    help="anneal: the headline line; batch / serve: the batched and served workloads")
     p.add_argument("--instances", type=int, default=64)
+    p.add_argument("--streams", type=int, default=32, help="batch mode: concurrent streams")
     p.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of the served trace")
     p.add_argument("--rate", type=float, default=20.0, help="mean arrivals per second")
     p.add_argument("--config", default="g63like")
@@ -248,6 +249,9 @@ def run_ours(args, rank, world, dist):
     variant_run = ann.stats()["variant"]
     if variant_run == 1:
         layout, kernel = "multi-spin coded (32 replicas per 32-bit word)", ("k_sweep_msc", args.threads or 256)
+    elif variant_run == 3:
+        layout = "multi-spin coded, a cluster of two CTAs per 32-replica word"
+        kernel = ("k_sweep_msc_pair", 256)
     else:
         fb = args.field_bits if args.field_bits else (7 if g.maxdeg <= 127 else 16)
         layout = {7: "packed byte (spin bit + 7-bit field)", 8: "int8 spin + int8 field",
@@ -359,7 +363,7 @@ def run_batch(args):
     cache = os.path.join(tempfile.gettempdir(), "pa_autotune_cache.json")
     t0 = time.perf_counter()
     opts, opts_b = [], []
-    cand = [c for c in autotune.CANDIDATES if c.get("variant") == 1 or c.get("field_bits") == 7]
+    cand = [c for c in autotune.CANDIDATES if c.get("variant") in (1, 3) or c.get("field_bits") == 7]
     for i, it in enumerate(inst):
         g = it["graph"]
         o, _ = autotune.tune(g, betas, it["R"], S, seed=it["seed"], steps=1, cache_path=cache, candidates=cand)
@@ -384,8 +388,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     plain_ms = ev0.elapsed_time(ev1)
     items = [(ann, betas, it["R"], S, it["seed"], K, o) for ann, it, o in zip(anns, inst, opts_b)]
-    B.pa_batch_anneal(items, n_streams=16, use_graph=True)   # warm-up (and graph build)
-    times = [B.pa_batch_anneal(items, n_streams=16, use_graph=True) for _ in range(max(args.steps, 1))]
+    B.pa_batch_anneal(items, n_streams=args.streams, use_graph=True)   # warm-up (and graph build)
+    times = [B.pa_batch_anneal(items, n_streams=args.streams, use_graph=True) for _ in range(max(args.steps, 1))]
     batch_ms = statistics.median(times)
     same = all(ann.best_record() == b for ann, b in zip(anns, plain_best))
     for a in anns:
@@ -398,7 +402,7 @@ def run_batch(args):
             "layouts_plain": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts)),
             "layouts_batched": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts_b)),
             "config": {"workload": "N~U[800,20000] random(p=12/(N-1))/torus/Delaunay, R 1024/4096/16384, "
-                                   "beta 0.1->3.0 K=200 S=4", "use_graph": True, "n_streams": 16}}
+                                   "beta 0.1->3.0 K=200 S=4", "use_graph": True, "n_streams": args.streams}}
     print(json.dumps(line), flush=True)
     return 0
 

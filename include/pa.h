@@ -56,6 +56,9 @@ typedef struct pa_ctx pa_ctx;
 #define PA_VARIANT_I8 0   /* int8 spins + int16/int8 local fields in shared memory */
 #define PA_VARIANT_MSC 1  /* multi-spin coded: 32 replicas per 32-bit word */
 #define PA_VARIANT_AUTO 2 /* chosen per graph by the built-in tuning table */
+#define PA_VARIANT_MSC_PAIR 3 /* multi-spin coded, one thread-block cluster of two
+                                 CTAs per 32-replica word (distributed shared
+                                 memory); same results as PA_VARIANT_MSC */
 
 typedef struct {
     int32_t variant;          /* PA_VARIANT_*; default PA_VARIANT_AUTO */

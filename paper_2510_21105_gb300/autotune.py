@@ -27,12 +27,13 @@ CANDIDATES = [
     dict(variant=0, field_bits=16, threads_per_cta=512, replicas_per_cta=8),
     dict(variant=1, threads_per_cta=256),
     dict(variant=1, threads_per_cta=128),
+    dict(variant=3),
 ]
 
 
 def feasible(g, cand) -> bool:
     fb = cand.get("field_bits", 0)
-    if cand.get("variant") == 1:
+    if cand.get("variant") in (1, 3):
         return g.maxdeg <= 127
     if fb in (7, 8) and g.maxdeg > 127:
         return False
@@ -62,6 +63,11 @@ def tune(g, betas, R, S, seed=0, steps=2, cache_path=None, candidates=None, cont
         if key in cache:
             return cache[key]["opts"], cache[key]["times"]
     cands = [c for c in (candidates or CANDIDATES) if feasible(g, c)]
+    if context != "alone":
+        # The CTA-pair kernel only gains by balancing one instance over the SMs;
+        # when other work fills the GPU that balance comes for free and its
+        # cluster barriers are pure cost.
+        cands = [c for c in cands if c.get("variant") != 3] or cands
     mid = max(0, len(betas) // 2 - steps)
     sl = list(betas[mid:mid + steps + 1])
     times = {}

@@ -20,7 +20,7 @@ _lib = None
 _lock = threading.Lock()
 
 PA_OK, PA_EINVAL, PA_ENOMEM, PA_ECUDA, PA_ETIMEOUT, PA_EBUSY, PA_ESTATE = 0, -1, -2, -3, -4, -5, -6
-PA_VARIANT_I8, PA_VARIANT_MSC, PA_VARIANT_AUTO = 0, 1, 2
+PA_VARIANT_I8, PA_VARIANT_MSC, PA_VARIANT_AUTO, PA_VARIANT_MSC_PAIR = 0, 1, 2, 3
 
 
 class PaError(RuntimeError):

@@ -17,6 +17,8 @@
 // sweep)) belongs to slot 4*(slot/4) + q.
 // The block is loaded from the parents chosen by the resampling (the copy of
 // the resampling is fused into this load) and written to the next buffers.
+#include <cooperative_groups.h>
+
 #include <mutex>
 #include <unordered_map>
 
@@ -603,6 +605,54 @@ __device__ __forceinline__ uint4 philox_from_shared(const PhiloxShared &p, uint3
     return c;
 }
 
+// One (position, word) item of a multi-spin-coded sweep: counts the frustrated
+// bonds of the 32 replicas, decides the 32 attempts and adds the energy change
+// of every accepted flip to Eacc (local or a cluster peer's shared memory).
+// Returns the mask of accepted replicas.
+template <int NPL, bool WEIGHTED>
+__device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t *Wsm, const uint32_t *T256, int p,
+                                             uint32_t x, uint32_t c3, int blk, int32_t *Eacc) {
+    const uint32_t e0 = __ldg(&a.g.rp[p]), e1 = __ldg(&a.g.rp[p + 1]);
+    const uint32_t vid = __ldg(&a.g.vid[p]);
+    uint32_t pl[NPL];
+#pragma unroll
+    for (int b = 0; b < NPL; ++b) pl[b] = 0u;
+    for (uint32_t e = e0; e < e1; ++e) {
+        uint32_t d = x ^ Wsm[__ldg(&a.g.col[e])];
+        if (WEIGHTED && __ldg(&a.g.wt[e]) < 0) d = ~d;
+#pragma unroll
+        for (int b = 0; b < NPL; ++b) {   // ripple-carry add of one bit per replica
+            const uint32_t carry = pl[b] & d;
+            pl[b] ^= d;
+            d = carry;
+        }
+    }
+    const uint32_t base = 128u - (e1 - e0);   // mb = 2c + 128 - deg
+    const PhiloxShared ps = philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1);
+    uint32_t acc32 = 0;
+#pragma unroll 2
+    for (int g = 0; g < 8; ++g) {
+        // Byte q of 2c: bit b of nibble g of plane b moved to bit 8q + b + 1
+        // (the multiply spreads the four bits, the mask keeps them).
+        uint32_t c2 = 0;
+#pragma unroll
+        for (int b = 0; b < NPL; ++b)
+            c2 |= (((pl[b] >> (4 * g)) & 0xFu) * (0x00204081u << (b + 1))) & (0x02020202u << b);
+        const uint32_t mb = c2 + base * 0x01010101u;
+        const uint4 u = philox_from_shared(ps, (uint32_t)(blk * 8 + g), a.key0, a.key1);
+        const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
+            if ((idx <= 128u) | (uu[q] < T256[idx])) {
+                acc32 |= 1u << (4 * g + q);
+                atomicAdd(&Eacc[4 * g + q], 2 * ((int)idx - 128));
+            }
+        }
+    }
+    return acc32;
+}
+
 template <int NPL, bool WEIGHTED, int NTB, int MINB>
 __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -655,45 +705,8 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
             for (int c = 0; c < a.g.ncol; ++c) {
                 const int p1 = cls[c + 1];
                 for (int p = cls[c] + tid; p < p1; p += NT) {
-                    const uint32_t e0 = __ldg(&a.g.rp[p]), e1 = __ldg(&a.g.rp[p + 1]);
                     const uint32_t x = Wsm[p];
-                    const uint32_t vid = __ldg(&a.g.vid[p]);
-                    uint32_t pl[NPL];
-#pragma unroll
-                    for (int b = 0; b < NPL; ++b) pl[b] = 0u;
-                    for (uint32_t e = e0; e < e1; ++e) {
-                        uint32_t d = x ^ Wsm[__ldg(&a.g.col[e])];
-                        if (WEIGHTED && __ldg(&a.g.wt[e]) < 0) d = ~d;
-#pragma unroll
-                        for (int b = 0; b < NPL; ++b) {   // ripple-carry add of one bit per replica
-                            const uint32_t carry = pl[b] & d;
-                            pl[b] ^= d;
-                            d = carry;
-                        }
-                    }
-                    const uint32_t base = 128u - (e1 - e0);   // mb = 2c + 128 - deg
-                    const PhiloxShared ps = philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1);
-                    uint32_t acc32 = 0;
-#pragma unroll 2
-                    for (int g = 0; g < 8; ++g) {
-                        // Byte q of 2c: bit b of nibble g of plane b moved to bit 8q + b + 1
-                        // (the multiply spreads the four bits, the mask keeps them).
-                        uint32_t c2 = 0;
-#pragma unroll
-                        for (int b = 0; b < NPL; ++b)
-                            c2 |= (((pl[b] >> (4 * g)) & 0xFu) * (0x00204081u << (b + 1))) & (0x02020202u << b);
-                        const uint32_t mb = c2 + base * 0x01010101u;
-                        const uint4 u = philox_from_shared(ps, (uint32_t)(blk * 8 + g), a.key0, a.key1);
-                        const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
-                            if ((idx <= 128u) | (uu[q] < T256[idx])) {
-                                acc32 |= 1u << (4 * g + q);
-                                atomicAdd(&Eacc[4 * g + q], 2 * ((int)idx - 128));
-                            }
-                        }
-                    }
+                    const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, Eacc);
                     if (acc32) {
                         Wsm[p] = x ^ acc32;
                         nacc += __popc(acc32 & vmask);
@@ -753,6 +766,143 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     }
 }
 
+// Multi-spin coding with a thread-block cluster of two CTAs per word. Both
+// CTAs keep a full copy of the word array; inside a colour class CTA r takes
+// the items at even (r = 0) or odd (r = 1) offsets, and every changed word is
+// stored into both copies (the peer's through distributed shared memory). A
+// cluster barrier closes each class. The 32 energies live in CTA 0, which
+// also does the best tracking; CTA 1 adds its energy changes there remotely.
+// Halving the work unit lets the SMs balance 2 x words CTAs dynamically.
+template <int NPL, bool WEIGHTED>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_pair(const SweepArgs a) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int rank = (int)cluster.block_rank();
+    extern __shared__ __align__(16) unsigned char smem[];
+    const bool act = !a.active || a.active[a.k];
+    const int nsweeps = act ? a.S : 0;
+    const int np = a.g.np, n = a.g.n;
+    uint32_t *Wsm = reinterpret_cast<uint32_t *>(smem);           // [np]
+    uint32_t *T256 = Wsm + np;                                      // [256] by m + 128
+    int32_t *cls = reinterpret_cast<int32_t *>(T256 + 256);
+    const int csz = (a.g.ncol + 1 + 3) & ~3;
+    int32_t *Eacc = cls + csz;      // [32] (used in CTA 0)
+    int32_t *PS = Eacc + 32;        // [32]
+    int32_t *misc = PS + 32;        // best E, step, sweep, slot, copy-from (r+1), changed
+    uint32_t *Wpeer = cluster.map_shared_rank(Wsm, rank ^ 1);
+    int32_t *E0 = cluster.map_shared_rank(Eacc, 0);
+
+    const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
+    const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
+    for (int i = tid; i < 256; i += NT) {
+        const int m = i - 128;
+        T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
+    }
+    for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
+
+    const int ncl = (int)(gridDim.x >> 1);
+    for (int blk = (int)(blockIdx.x >> 1); blk < a.nblk; blk += ncl) {   // uniform within the cluster
+        const int slot0 = blk * 32;
+        if (tid < 32) PS[tid] = act ? a.parent[slot0 + tid] : slot0 + tid;
+        if (tid == 0) {
+            const int4 br = a.best_rec[blk];
+            misc[0] = br.x; misc[1] = br.y; misc[2] = br.z; misc[3] = br.w;
+            misc[4] = 0; misc[5] = 0;
+        }
+        __syncthreads();
+        if (tid < 32 && rank == 0) Eacc[tid] = a.E_in[PS[tid]];
+        for (int c = tid; c < (np >> 2); c += NT) {
+            uint32_t w4[4] = {0u, 0u, 0u, 0u};
+            for (int r = 0; r < 32; ++r) {
+                const uint32_t v = __ldg(reinterpret_cast<const uint32_t *>(a.spins_in + (size_t)PS[r] * np + 4 * c));
+#pragma unroll
+                for (int j = 0; j < 4; ++j) w4[j] |= ((((v >> (8 * j)) & 0xFFu) == 1u) ? 1u : 0u) << r;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) Wsm[4 * c + j] = w4[j];
+        }
+        cluster.sync();   // both copies loaded, energies in place
+        uint32_t vmask = 0xFFFFFFFFu;
+        if (slot0 + 32 > a.R) vmask = a.R > slot0 ? (0xFFFFFFFFu >> (32 - (a.R - slot0))) : 0u;
+        uint32_t nacc = 0;
+        for (int s = 0; s < nsweeps; ++s) {
+            const uint32_t c3 = TAG_SWEEP | (uint32_t)s;
+            for (int c = 0; c < a.g.ncol; ++c) {
+                const int p1 = cls[c + 1];
+                for (int p = cls[c] + 2 * tid + rank; p < p1; p += 2 * NT) {
+                    const uint32_t x = Wsm[p];
+                    const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, E0);
+                    if (acc32) {
+                        Wsm[p] = x ^ acc32;
+                        Wpeer[p] = x ^ acc32;
+                        nacc += __popc(acc32 & vmask);
+                    }
+                }
+                cluster.sync();
+            }
+            if (rank == 0 && tid == 0) {
+                int bq = -1, bE = 0x7FFFFFFF;
+                for (int q = 0; q < 32; ++q)
+                    if (slot0 + q < a.R && Eacc[q] < bE) { bE = Eacc[q]; bq = q; }
+                misc[4] = 0;
+                if (bq >= 0) {
+                    atomicMin(&a.sweep_emin[(size_t)a.k * a.S + s], bE);
+                    if (bE < misc[0]) {
+                        misc[0] = bE; misc[1] = a.k; misc[2] = s; misc[3] = slot0 + bq;
+                        misc[4] = bq + 1; misc[5] = 1;
+                    }
+                }
+            }
+            __syncthreads();
+            if (misc[4]) {   // CTA 0 only (CTA 1 never sets it)
+                const int rq = misc[4] - 1;
+                uint32_t *dst = reinterpret_cast<uint32_t *>(a.best_cfg + (size_t)blk * np);
+                for (int c = tid; c < (np >> 2); c += NT) {
+                    uint32_t v = 0;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const bool real = 4 * c + j < n;
+                        v |= (real ? (((Wsm[4 * c + j] >> rq) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
+                    }
+                    dst[c] = v;
+                }
+            }
+            cluster.sync();   // the copy reads CTA 0's words before the next sweep changes them
+        }
+        // Store: each CTA writes half of the columns from its own (complete) copy.
+        for (int c = 2 * tid + rank; c < (np >> 2); c += 2 * NT) {
+            uint32_t w4[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) w4[j] = Wsm[4 * c + j];
+            for (int r = 0; r < 32; ++r) {
+                uint32_t v = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const bool real = 4 * c + j < n;
+                    v |= (real ? (((w4[j] >> r) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
+                }
+                *reinterpret_cast<uint32_t *>(a.spins_out + (size_t)(slot0 + r) * np + 4 * c) = v;
+            }
+        }
+        if (rank == 0) {
+            if (tid < 32) a.E_out[slot0 + tid] = Eacc[tid];
+            if (tid == 0 && misc[5]) a.best_rec[blk] = make_int4(misc[0], misc[1], misc[2], misc[3]);
+        }
+        const uint32_t wsum = __reduce_add_sync(0xFFFFFFFFu, nacc);
+        if (act && lane == 0 && wsum) atomicAdd(&a.accepts[a.k], (unsigned long long)wsum);
+        cluster.sync();   // neither copy is reused before both CTAs are done with this word
+    }
+}
+
+template <bool W>
+void *msc_pair_kernel(int mmax) {
+    if (mmax <= 7) return reinterpret_cast<void *>(&k_sweep_msc_pair<3, W>);
+    if (mmax <= 15) return reinterpret_cast<void *>(&k_sweep_msc_pair<4, W>);
+    if (mmax <= 31) return reinterpret_cast<void *>(&k_sweep_msc_pair<5, W>);
+    if (mmax <= 63) return reinterpret_cast<void *>(&k_sweep_msc_pair<6, W>);
+    return reinterpret_cast<void *>(&k_sweep_msc_pair<7, W>);
+}
+
 template <bool W>
 void *msc_kernel(int mmax) {
     if (mmax <= 7) return reinterpret_cast<void *>(&k_sweep_msc<3, W, 256, 4>);
@@ -780,6 +930,7 @@ void *kernel_ptr() {
 
 void *select_kernel(int G, int fb, bool weighted, int threads, int mmax) {
     if (fb == 1) return weighted ? msc_kernel<true>(mmax) : msc_kernel<false>(mmax);
+    if (fb == 2) return weighted ? msc_pair_kernel<true>(mmax) : msc_pair_kernel<false>(mmax);
     if (fb == 7) return weighted ? packed_kernel<true>(threads) : packed_kernel<false>(threads);
     if (G == 1) {
         if (fb == 16) return weighted ? kernel_ptr<1, 16, true>() : kernel_ptr<1, 16, false>();
@@ -794,8 +945,9 @@ void *select_kernel(int G, int fb, bool weighted, int threads, int mmax) {
 cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int threads,
                             bool weighted, SweepConfig *cfg) {
     size_t smem;
-    if (field_bits == 1) {   // multi-spin coded: 32 replicas per word
+    if (field_bits == 1 || field_bits == 2) {   // multi-spin coded: 32 replicas per word (2: CTA pairs)
         G = 8;
+        threads = 256;
         smem = (size_t)g.np * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + (32 + 32 + 8) * 4;
     } else if (field_bits == 7) {
         G = 1;
@@ -825,10 +977,27 @@ cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int
     int dev = 0, sms = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nblk = (R + 4 * G - 1) / (4 * G);
+    if (field_bits == 2) {
+        // One cluster of two CTAs per word; the hardware schedules them as slots free up.
+        cudaLaunchConfig_t lc = {};
+        lc.gridDim = dim3(2 * nblk);
+        lc.blockDim = dim3(threads);
+        lc.dynamicSmemBytes = smem;
+        int ncl = 0;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&ncl, fn, &lc);
+        if (e != cudaSuccess) return e;
+        if (ncl < 1) return cudaErrorInvalidConfiguration;
+        cfg->G = G;
+        cfg->field_bits = field_bits;
+        cfg->threads = threads;
+        cfg->smem = smem;
+        cfg->grid = 2 * nblk;
+        return cudaSuccess;
+    }
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    const int nblk = (R + 4 * G - 1) / (4 * G);
     cfg->G = G;
     cfg->field_bits = field_bits;
     cfg->threads = threads;

@@ -238,16 +238,17 @@ void collect_events(RunState &r) {
 }
 
 int validate_opts(pa_ctx *c, const pa_anneal_opts &o) {
-    if (o.variant < 0 || o.variant > 2) return fail(c, PA_EINVAL, "variant");
+    if (o.variant < 0 || o.variant > 3) return fail(c, PA_EINVAL, "variant");
     if (o.field_bits != 16 && o.field_bits != 8 && o.field_bits != 7)
         return fail(c, PA_EINVAL, "field_bits must be 0, 16, 8 or 7");
     if (o.field_bits != 16 && c->maxdeg > 127)
         return fail(c, PA_EINVAL, "8- and 7-bit fields need max degree <= 127");
     if (o.field_bits == 7 && !c->packed_ok)
         return fail(c, PA_EINVAL, "the packed layout needs n <= 32720");
-    if (o.variant == PA_VARIANT_MSC && c->maxdeg > 127)
+    const bool msc = o.variant == PA_VARIANT_MSC || o.variant == PA_VARIANT_MSC_PAIR;
+    if (msc && c->maxdeg > 127)
         return fail(c, PA_EINVAL, "the multi-spin-coded variant needs max degree <= 127");
-    if (o.variant == PA_VARIANT_MSC && o.threads_per_cta > 256)
+    if (msc && o.threads_per_cta > 256)
         return fail(c, PA_EINVAL, "the multi-spin-coded variant runs at most 256 threads per CTA");
     if (o.nlm_period < 0) return fail(c, PA_EINVAL, "nlm_period < 0");
     if (o.nlm_kind != 0 && o.nlm_kind != 1) return fail(c, PA_EINVAL, "nlm_kind must be 0 or 1");
@@ -484,13 +485,24 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     if (opts) o = *opts;
     if (o.variant == PA_VARIANT_AUTO) {
         // Multi-spin coding is fastest once its 32-replica blocks fill the GPU
-        // (two per SM); otherwise the 4-replica layouts give more blocks.
+        // (two per SM); otherwise the 4-replica layouts give more blocks. With
+        // few, large colour classes (tori: two) the per-class cluster barrier
+        // is cheap and the CTA-pair kernel's finer work unit wins (measured:
+        // 100x100 torus, R = 32768: 595 vs 516 G attempts/s); with many small
+        // classes (G63-shaped: nine) the single-CTA kernel is as fast or faster.
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const bool msc_fills = (R + 31) / 32 >= 2 * (sms > 0 ? sms : 152);
-        o.variant = (c->maxdeg <= 127 && msc_fills && o.field_bits == 0 &&
-                     (o.threads_per_cta == 0 || o.threads_per_cta <= 256)) ? PA_VARIANT_MSC : PA_VARIANT_I8;
+        if (sms <= 0) sms = 152;
+        const int32_t words = (R + 31) / 32;
+        const bool msc_ok = c->maxdeg <= 127 && o.field_bits == 0 &&
+                            (o.threads_per_cta == 0 || o.threads_per_cta <= 256);
+        if (msc_ok && c->ncol <= 4 && words >= sms)
+            o.variant = PA_VARIANT_MSC_PAIR;
+        else if (msc_ok && words >= 2 * sms)
+            o.variant = PA_VARIANT_MSC;
+        else
+            o.variant = PA_VARIANT_I8;
     }
     if (o.field_bits == 0) o.field_bits = (c->maxdeg <= 127 && c->packed_ok) ? 7 : 16;
     if (K < 0 || R < 1 || R > 65536 || sweeps < 0 || sweeps >= (1 << 28))
@@ -519,13 +531,14 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     r.k_done = 0;
     r.launches = r.sweep_launches = 0;
     r.anneal_ms = r.sweep_ms = 0.0;
-    r.variant = o.variant == PA_VARIANT_MSC ? PA_VARIANT_MSC : PA_VARIANT_I8;
+    r.variant = o.variant == PA_VARIANT_AUTO ? PA_VARIANT_I8 : o.variant;
     // Sweep kernel shape.
-    const bool msc = o.variant == PA_VARIANT_MSC;
+    const bool msc = o.variant == PA_VARIANT_MSC || o.variant == PA_VARIANT_MSC_PAIR;
     int G = o.replicas_per_cta == 8 ? 2 : 1;
     int threads = o.threads_per_cta ? o.threads_per_cta : (msc ? 256 : (o.field_bits == 7 ? 128 : 512));
     pa::GraphDev g = c->gdev();
-    cudaError_t ce = pa::sweep_configure(g, R, G, msc ? 1 : o.field_bits, threads, c->weighted, &r.sweep);
+    const int fcode = o.variant == PA_VARIANT_MSC_PAIR ? 2 : (msc ? 1 : o.field_bits);
+    cudaError_t ce = pa::sweep_configure(g, R, G, fcode, threads, c->weighted, &r.sweep);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "sweep_configure");
     G = r.sweep.G;
     r.Rpad = ((R + 4 * G - 1) / (4 * G)) * 4 * G;

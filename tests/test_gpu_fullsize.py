@@ -44,13 +44,13 @@ def _replay_check(g, betas, R, S, seed, k, subset, nlm_period=0, nlm_block=0, **
     return E_a
 
 
-@pytest.mark.parametrize("field_bits", [0, 16])
-def test_replay_g63like_full_population(field_bits):
+@pytest.mark.parametrize("field_bits,variant", [(0, 2), (16, 0), (0, 1), (0, 3)])
+def test_replay_g63like_full_population(field_bits, variant):
     c = wl.CONFIGS["g63like"]
     g = c["graph"]()
     betas = wl.linear_betas(*c["beta"], c["K"])
     subset = np.array([0, 1, 2, 3, 4097, 8190, 12345, 16383])
-    _replay_check(g, betas, c["R"], c["S"], c["seed"], 3, subset, field_bits=field_bits)
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], 3, subset, field_bits=field_bits, variant=variant)
 
 
 def test_replay_g63like_nonlocal_step():
@@ -74,7 +74,7 @@ def test_replay_g63like_block_move_step():
     _replay_check(g, betas, c["R"], c["S"], c["seed"], k, subset, nlm_period=k, nlm_block=32)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 3])
 def test_replay_torus100_full_population(variant):
     c = wl.CONFIGS["torus100"]
     g = c["graph"]()

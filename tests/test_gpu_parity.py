@@ -31,7 +31,7 @@ def test_tables_and_colouring_match_oracle():
     a.close()
 
 
-@pytest.mark.parametrize("field_bits,variant", [(0, 0), (16, 0), (0, 1)])
+@pytest.mark.parametrize("field_bits,variant", [(0, 0), (16, 0), (0, 1), (0, 3)])
 def test_parity_gnp800_full_workload(field_bits, variant):
     # N = 800, p = 0.06, R = 256, beta 0.1 -> 3.0 in 100 steps, 4 sweeps, seed 0.
     c = wl.CONFIGS["gnp800"]
@@ -55,7 +55,8 @@ def _oracle_cached(key, fn):
                                     (1, {}), (1, {"field_bits": 16}), (7, {"field_bits": 7, "threads_per_cta": 256}),
                                     (24, {"replicas_per_cta": 8, "field_bits": 16}),
                                     (40, {"replicas_per_cta": 8, "field_bits": 8, "threads_per_cta": 128}),
-                                    (6, {"variant": 1}), (33, {"variant": 1}), (70, {"variant": 1, "threads_per_cta": 128})])
+                                    (6, {"variant": 1}), (33, {"variant": 1}), (70, {"variant": 1, "threads_per_cta": 128}),
+                                    (1, {"variant": 3}), (40, {"variant": 3}), (97, {"variant": 3})])
 def test_parity_ragged_signed(R, opts):
     g = wl.from_edges(37, *_random_edges(37, 90, seed=R), name="ragged")
     betas = wl.linear_betas(0.05, 2.5, 7)
@@ -76,7 +77,7 @@ def _random_edges(n, m, seed):
     return e[:, 0], e[:, 1], w
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 3])
 def test_parity_torus_two_colour_checkerboard(variant):
     g = wl.torus(24, seed=5)
     betas = wl.linear_betas(0.1, 3.5, 12)
@@ -86,7 +87,7 @@ def test_parity_torus_two_colour_checkerboard(variant):
     assert_parity(gpu, orc, g, 64, 4)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 3])
 def test_parity_nonlocal_moves(variant):
     g = wl.gnm(500, 3000, seed=7)
     betas = wl.linear_betas(0.1, 3.0, 13)
@@ -97,7 +98,8 @@ def test_parity_nonlocal_moves(variant):
 
 
 @pytest.mark.parametrize("block", [1, 13, 300])
-@pytest.mark.parametrize("variant,field_bits", [(0, 16), (0, 7), (1, 0)], ids=["int16", "packed", "msc"])
+@pytest.mark.parametrize("variant,field_bits", [(0, 16), (0, 7), (1, 0), (3, 0)],
+                         ids=["int16", "packed", "msc", "msc-pair"])
 def test_parity_block_moves(variant, field_bits, block):
     """Block moves (nlm_kind = 1) on a signed graph in every layout: b = 1 is
     a single Metropolis flip, b = 300 covers the seed's whole component."""
@@ -121,7 +123,7 @@ def test_parity_block_moves_adaptive():
     assert_parity(gpu, orc, g, 64, 2)
 
 
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 3])
 def test_parity_acceptance_rate_control(variant):
     """adaptive = 2 (acceptance-rate rule), alone and with block moves."""
     g = wl.from_edges(250, *_random_edges(250, 1000, seed=58))
@@ -134,7 +136,8 @@ def test_parity_acceptance_rate_control(variant):
         assert_parity(gpu, orc, g, 72, 2)
 
 
-@pytest.mark.parametrize("variant,field_bits", [(0, 16), (0, 7), (1, 0)], ids=["int16", "packed", "msc"])
+@pytest.mark.parametrize("variant,field_bits", [(0, 16), (0, 7), (1, 0), (3, 0)],
+                         ids=["int16", "packed", "msc", "msc-pair"])
 def test_parity_stagnation_reheating(variant, field_bits):
     """Stagnation reheating on a fixed schedule, alone and with block moves;
     the schedule index of every step is compared."""
@@ -200,9 +203,10 @@ def test_degenerate_cases():
 @pytest.mark.parametrize("kw,K,split", [
     (dict(nlm_period=4), 10, 6),
     (dict(variant=1), 10, 3),
+    (dict(variant=3, nlm_period=3), 10, 4),
     (dict(adaptive=1, rho=0.5, adapt_J=4, adapt_dbeta_max=0.3, beta_max=1.5, nlm_period=3), 40, 7),
     (dict(reheat_after=2, reheat_back=3, nlm_period=2, nlm_kind=1, nlm_block=4), 24, 11),
-], ids=["fixed-nlm", "msc", "adaptive", "reheat-block"])
+], ids=["fixed-nlm", "msc", "msc-pair", "adaptive", "reheat-block"])
 def test_checkpoint_resume_is_bit_exact(tmp_path, kw, K, split):
     """A run saved after `split` steps and resumed in a fresh context equals
     the uninterrupted run: population, best record and every per-step record
@@ -250,12 +254,13 @@ def test_repeat_runs_are_identical_and_launch_shape_free():
         assert np.array_equal(r1["spins"], r["spins"]) and r1["best"] == r["best"]
 
 
-def test_parity_msc_many_words_ragged_last_word():
+@pytest.mark.parametrize("variant", [1, 3])
+def test_parity_msc_many_words_ragged_last_word(variant):
     # R = 4937: 155 words of 32 replicas (more words than SMs, so blocks loop
     # over words) with 9 live replicas in the last one; signed weights and
     # non-local moves.
     g = wl.from_edges(300, *_random_edges(300, 1500, seed=99))
     betas = wl.linear_betas(0.1, 2.5, 6)
-    gpu = run_gpu(g, betas, 4937, 2, seed=31, variant=1, nlm_period=2)
+    gpu = run_gpu(g, betas, 4937, 2, seed=31, variant=variant, nlm_period=2)
     orc = run_oracle(g, betas, 4937, 2, seed=31, nlm_period=2)
     assert_parity(gpu, orc, g, 4937, 2)
