@@ -545,15 +545,17 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
 
 // ---------------------------------------------------------------------------
 // Multi-spin-coded variant: W[p] holds the spins of 32 replicas (slots
-// 32*blk .. 32*blk+31) at position p, bit r = 1 for +1. No fields are kept:
+// 32*blk .. 32*blk+31) at position p, 1 for +1. Replica 4g + q (group g of
+// the Philox call that serves it, word q) sits at bit 8q + g, so that a
+// group's four replicas are one bit of each byte. No fields are kept:
 // an item (p, word) XORs its word with each neighbour's word (and with all
 // ones for a -1 weight), so bit r of d_j is 1 iff the bond (p, j) contributes
 // +1 to m_r = -x_p h_p; a bit-sliced counter over the neighbours gives c_r and
 // m_r = 2 c_r - deg(p). Groups of four replicas are spread to bytes and
 // decided exactly like the packed layout (same thresholds, same Philox word
 // (vertex, slot/4, step, sweep)). Accepted replicas flip with one XOR.
-__device__ __forceinline__ uint32_t spread_nibble(uint32_t nib) {   // bit q -> bit 8q
-    return (nib * 0x00204081u) & 0x01010101u;
+__device__ __forceinline__ int msc_bit(int r) {   // bit of replica r = 4g + q in a word
+    return 8 * (r & 3) + (r >> 2);
 }
 
 // Philox4x32-10 for the eight counters (c0, c1_g, c2, c3) of one item, which
@@ -627,27 +629,31 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
             d = carry;
         }
     }
-    const uint32_t base = 128u - (e1 - e0);   // mb = 2c + 128 - deg
+    const uint32_t deg = e1 - e0;
+    const uint32_t base = 128u - deg;   // mb = 2c + 128 - deg
     const PhiloxShared ps = philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1);
     uint32_t acc32 = 0;
-#pragma unroll 2
+#pragma unroll
     for (int g = 0; g < 8; ++g) {
-        // Byte q of 2c: bit b of nibble g of plane b moved to bit 8q + b + 1
-        // (the multiply spreads the four bits, the mask keeps them).
+        // Byte q of 2c for group g: bit 8q + g of plane b rotated to bit 8q + b + 1.
         uint32_t c2 = 0;
 #pragma unroll
         for (int b = 0; b < NPL; ++b)
-            c2 |= (((pl[b] >> (4 * g)) & 0xFu) * (0x00204081u << (b + 1))) & (0x02020202u << b);
+            c2 |= __funnelshift_r(pl[b], pl[b], (uint32_t)(g - b - 1) & 31u) & (0x02020202u << b);
         const uint32_t mb = c2 + base * 0x01010101u;
         const uint4 u = philox_from_shared(ps, (uint32_t)(blk * 8 + g), a.key0, a.key1);
         const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+        uint32_t ag = 0;   // acceptances of the group, one bit per byte
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
-            if ((idx <= 128u) | (uu[q] < T256[idx])) {
-                acc32 |= 1u << (4 * g + q);
-                atomicAdd(&Eacc[4 * g + q], 2 * ((int)idx - 128));
-            }
+            ag |= (uint32_t)((idx <= 128u) | (uu[q] < T256[idx])) << (8 * q);
+        }
+        acc32 |= ag << g;
+        if (ag) {   // energy change 2m = 2(mb byte - 128) of each accepted replica
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if ((ag >> (8 * q)) & 1u) atomicAdd(&Eacc[4 * g + q], 2 * ((int)((mb >> (8 * q)) & 0xFFu) - 128));
         }
     }
     return acc32;
@@ -691,14 +697,14 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
             for (int r = 0; r < 32; ++r) {
                 const uint32_t v = __ldg(reinterpret_cast<const uint32_t *>(a.spins_in + (size_t)PS[r] * np + 4 * c));
 #pragma unroll
-                for (int j = 0; j < 4; ++j) w4[j] |= ((((v >> (8 * j)) & 0xFFu) == 1u) ? 1u : 0u) << r;
+                for (int j = 0; j < 4; ++j) w4[j] |= ((((v >> (8 * j)) & 0xFFu) == 1u) ? 1u : 0u) << msc_bit(r);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) Wsm[4 * c + j] = w4[j];
         }
         __syncthreads();
-        uint32_t vmask = 0xFFFFFFFFu;
-        if (slot0 + 32 > a.R) vmask = a.R > slot0 ? (0xFFFFFFFFu >> (32 - (a.R - slot0))) : 0u;
+        uint32_t vmask = 0u;   // bits of the live replicas
+        for (int r = 0; r < 32; ++r) vmask |= (slot0 + r < a.R ? 1u : 0u) << msc_bit(r);
         uint32_t nacc = 0;
         for (int s = 0; s < nsweeps; ++s) {
             const uint32_t c3 = TAG_SWEEP | (uint32_t)s;
@@ -736,7 +742,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const bool real = 4 * c + j < n;
-                        v |= (real ? (((Wsm[4 * c + j] >> rq) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
+                        v |= (real ? (((Wsm[4 * c + j] >> msc_bit(rq)) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
                     }
                     dst[c] = v;
                 }
@@ -753,7 +759,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const bool real = 4 * c + j < n;
-                    v |= (real ? (((w4[j] >> r) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
+                    v |= (real ? (((w4[j] >> msc_bit(r)) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
                 }
                 *reinterpret_cast<uint32_t *>(a.spins_out + (size_t)(slot0 + r) * np + 4 * c) = v;
             }
@@ -816,14 +822,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
             for (int r = 0; r < 32; ++r) {
                 const uint32_t v = __ldg(reinterpret_cast<const uint32_t *>(a.spins_in + (size_t)PS[r] * np + 4 * c));
 #pragma unroll
-                for (int j = 0; j < 4; ++j) w4[j] |= ((((v >> (8 * j)) & 0xFFu) == 1u) ? 1u : 0u) << r;
+                for (int j = 0; j < 4; ++j) w4[j] |= ((((v >> (8 * j)) & 0xFFu) == 1u) ? 1u : 0u) << msc_bit(r);
             }
 #pragma unroll
             for (int j = 0; j < 4; ++j) Wsm[4 * c + j] = w4[j];
         }
         cluster.sync();   // both copies loaded, energies in place
-        uint32_t vmask = 0xFFFFFFFFu;
-        if (slot0 + 32 > a.R) vmask = a.R > slot0 ? (0xFFFFFFFFu >> (32 - (a.R - slot0))) : 0u;
+        uint32_t vmask = 0u;   // bits of the live replicas
+        for (int r = 0; r < 32; ++r) vmask |= (slot0 + r < a.R ? 1u : 0u) << msc_bit(r);
         uint32_t nacc = 0;
         for (int s = 0; s < nsweeps; ++s) {
             const uint32_t c3 = TAG_SWEEP | (uint32_t)s;
@@ -862,7 +868,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const bool real = 4 * c + j < n;
-                        v |= (real ? (((Wsm[4 * c + j] >> rq) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
+                        v |= (real ? (((Wsm[4 * c + j] >> msc_bit(rq)) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
                     }
                     dst[c] = v;
                 }
@@ -879,7 +885,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const bool real = 4 * c + j < n;
-                    v |= (real ? (((w4[j] >> r) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
+                    v |= (real ? (((w4[j] >> msc_bit(r)) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
                 }
                 *reinterpret_cast<uint32_t *>(a.spins_out + (size_t)(slot0 + r) * np + 4 * c) = v;
             }
