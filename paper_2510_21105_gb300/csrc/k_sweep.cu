@@ -681,7 +681,8 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     }
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
 
-    for (int blk = blockIdx.x; blk < a.nblk; blk += gridDim.x) {
+    for (int lb = blockIdx.x; lb < a.nblk; lb += gridDim.x) {
+        const int blk = a.blk_base + lb;
         const int slot0 = blk * 32;
         if (tid < 32) PS[tid] = act ? a.parent[slot0 + tid] : slot0 + tid;
         if (tid == 0) {
@@ -807,7 +808,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
 
     const int ncl = (int)(gridDim.x >> 1);
-    for (int blk = (int)(blockIdx.x >> 1); blk < a.nblk; blk += ncl) {   // uniform within the cluster
+    for (int lb = (int)(blockIdx.x >> 1); lb < a.nblk; lb += ncl) {   // uniform within the cluster
+        const int blk = a.blk_base + lb;
         const int slot0 = blk * 32;
         if (tid < 32) PS[tid] = act ? a.parent[slot0 + tid] : slot0 + tid;
         if (tid == 0) {

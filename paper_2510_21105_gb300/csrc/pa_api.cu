@@ -94,6 +94,16 @@ struct DevBuf {
 struct RunState {
     bool begun = false;
     int32_t R = 0, Rpad = 0, K = 0, S = 0, nblk = 0, nch = 0, k_done = 0;
+    int32_t nrec = 0;                    // replica blocks in all (one best record each)
+    // Multi-spin coding with a word count that the SM count does not divide:
+    // the first (words / SMs) * SMs words run in the one-CTA kernel and the
+    // rest in the CTA-pair kernel on a second stream, concurrently, so every
+    // SM carries the same share.
+    bool split = false;
+    pa::SweepConfig sweep2{};
+    int32_t nblk2 = 0, blk_base2 = 0;
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     uint64_t seed = 0;
     pa_anneal_opts opts{};
     std::vector<double> betas;           // per step (fixed schedule)
@@ -473,6 +483,13 @@ void pa_destroy(pa_ctx *ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream());
     free_run_events(ctx->run);
+    RunState &r = ctx->run;
+    if (r.st2) {
+        cudaStreamSynchronize(r.st2);
+        cudaStreamDestroy(r.st2);
+    }
+    if (r.ev_fork) cudaEventDestroy(r.ev_fork);
+    if (r.ev_join) cudaEventDestroy(r.ev_join);
     cudaGetLastError();
     delete ctx;   // buffers return to the memory pool
 }
@@ -543,6 +560,30 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     G = r.sweep.G;
     r.Rpad = ((R + 4 * G - 1) / (4 * G)) * 4 * G;
     r.nblk = r.Rpad / (4 * G);
+    r.nrec = r.nblk;
+    r.split = false;
+    if (o.variant == PA_VARIANT_MSC) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int32_t words = r.nblk, wm = sms > 0 ? (words / sms) * sms : 0;
+        if (wm > 0 && wm < words) {
+            ce = pa::sweep_configure(g, R - 32 * wm, 8, 2, 256, c->weighted, &r.sweep2);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "sweep_configure (tail)");
+            ce = pa::sweep_configure(g, 32 * wm, 8, 1, threads, c->weighted, &r.sweep);
+            if (ce != cudaSuccess) return cuda_fail(c, ce, "sweep_configure (head)");
+            if (!r.st2 && cudaStreamCreateWithFlags(&r.st2, cudaStreamNonBlocking) != cudaSuccess)
+                return fail(c, PA_ECUDA, "stream create");
+            if (!r.ev_fork && cudaEventCreateWithFlags(&r.ev_fork, cudaEventDisableTiming) != cudaSuccess)
+                return fail(c, PA_ECUDA, "event create");
+            if (!r.ev_join && cudaEventCreateWithFlags(&r.ev_join, cudaEventDisableTiming) != cudaSuccess)
+                return fail(c, PA_ECUDA, "event create");
+            r.split = true;
+            r.nblk = wm;
+            r.nblk2 = words - wm;
+            r.blk_base2 = wm;
+        }
+    }
     r.nch = (R + pa::RS_CHUNK - 1) / pa::RS_CHUNK;
     const int32_t mmax = c->maxdeg;
     // Host tables.
@@ -601,8 +642,8 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
               r.rec_o.alloc(4 * (size_t)Kc, ST) && r.rec_acc.alloc(8 * (size_t)Kc, ST) &&
               r.rec_sweep.alloc(4 * (size_t)Kc * Sc, ST) && r.rec_stamp.alloc(8 * (size_t)(Kc + 1), ST) &&
               r.rec_nlm_pairs.alloc(4 * (size_t)Kc, ST) && r.rec_nlm_flips.alloc(8 * (size_t)Kc, ST) &&
-              r.rec_jsel.alloc(4 * (size_t)Kc, ST) && r.best_rec.alloc(16 * (size_t)r.nblk, ST) &&
-              r.best_cfg.alloc((size_t)r.nblk * c->np, ST);
+              r.rec_jsel.alloc(4 * (size_t)Kc, ST) && r.best_rec.alloc(16 * (size_t)r.nrec, ST) &&
+              r.best_cfg.alloc((size_t)r.nrec * c->np, ST);
     if (ok && o.record_counts) ok = r.rec_counts.alloc(4 * (size_t)Kc * R, ST);
     if (ok && o.adaptive)
         ok = r.ad_state.alloc(16, ST) && r.ad_qsel.alloc(4 * (size_t)Kc, ST) && r.ad_active.alloc(4 * (size_t)Kc, ST) &&
@@ -625,8 +666,8 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
         std::vector<int32_t> ident(r.Rpad);
         for (int32_t s = 0; s < r.Rpad; ++s) ident[s] = s;
         PA_CUDA(c, copy(c, r.parent.p, ident.data(), 4 * (size_t)r.Rpad, cudaMemcpyHostToDevice, st, true));
-        std::vector<int4> br(r.nblk, make_int4(0x7FFFFFFF, -1, -1, -1));
-        PA_CUDA(c, copy(c, r.best_rec.p, br.data(), 16 * (size_t)r.nblk, cudaMemcpyHostToDevice, st, true));
+        std::vector<int4> br(r.nrec, make_int4(0x7FFFFFFF, -1, -1, -1));
+        PA_CUDA(c, copy(c, r.best_rec.p, br.data(), 16 * (size_t)r.nrec, cudaMemcpyHostToDevice, st, true));
         // Pageable sources: wait before the vectors go out of scope.
         PA_CUDA(c, cudaStreamSynchronize(st));
     }
@@ -640,7 +681,7 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     PA_CUDA(c, cudaMemsetAsync(r.rec_nlm_pairs.p, 0, 4 * (size_t)Kc, st));
     PA_CUDA(c, cudaMemsetAsync(r.rec_nlm_flips.p, 0, 8 * (size_t)Kc, st));
     PA_CUDA(c, cudaMemsetAsync(r.rec_jsel.p, 0xFF, 4 * (size_t)Kc, st));
-    PA_CUDA(c, cudaMemsetAsync(r.best_cfg.p, 0, (size_t)r.nblk * c->np, st));
+    PA_CUDA(c, cudaMemsetAsync(r.best_cfg.p, 0, (size_t)r.nrec * c->np, st));
     if (o.record_counts) PA_CUDA(c, cudaMemsetAsync(r.rec_counts.p, 0, 4 * (size_t)Kc * R, st));
     if (o.reheat_after > 0) {
         PA_CUDA(c, cudaMemsetAsync(r.ad_state.p, 0, 16, st));
@@ -777,7 +818,18 @@ int enqueue_step(pa_ctx *c, int32_t k, cudaStream_t st, bool time_sweep) {
         r.ev_sweep.push_back(s1);
         PA_CUDA(c, cudaEventRecord(s0, st));
     }
+    if (r.split) {   // fork: the tail words run on the second stream
+        PA_CUDA(c, cudaEventRecord(r.ev_fork, st));
+        PA_CUDA(c, cudaStreamWaitEvent(r.st2, r.ev_fork, 0));
+        pa::SweepArgs sb = sa;
+        sb.nblk = r.nblk2;
+        sb.blk_base = r.blk_base2;
+        PA_CUDA(c, pa::launch_sweep(r.sweep2, sb, r.st2));
+        PA_CUDA(c, cudaEventRecord(r.ev_join, r.st2));
+        r.launches += 1;
+    }
     PA_CUDA(c, pa::launch_sweep(r.sweep, sa, st));
+    if (r.split) PA_CUDA(c, cudaStreamWaitEvent(st, r.ev_join, 0));
     if (time_sweep) PA_CUDA(c, cudaEventRecord(s1, st));
     r.launches += 1;
     r.sweep_launches += 1;
@@ -855,13 +907,13 @@ namespace {
 // Lexicographic minimum of the per-block records; returns the block or -1.
 int best_block(pa_ctx *c, int4 *rec) {
     RunState &r = c->run;
-    std::vector<int4> br(r.nblk);
-    if (copy(c, br.data(), r.best_rec.p, 16 * (size_t)r.nblk, cudaMemcpyDeviceToHost) != cudaSuccess) {
+    std::vector<int4> br(r.nrec);
+    if (copy(c, br.data(), r.best_rec.p, 16 * (size_t)r.nrec, cudaMemcpyDeviceToHost) != cudaSuccess) {
         cudaGetLastError();
         return -2;
     }
     int best = -1;
-    for (int b = 0; b < r.nblk; ++b) {
+    for (int b = 0; b < r.nrec; ++b) {
         if (br[b].y < 0) continue;
         if (best < 0) { best = b; continue; }
         const int4 &x = br[b], &y = br[best];

@@ -81,9 +81,10 @@ struct SweepArgs {
     const uint32_t *tables;      // [ntables][mmax+1] acceptance thresholds
     const int32_t *tidx;         // [K] table used by step k
     const int32_t *active;       // [K] 0 = skip the step (adaptive end), may be null
-    int32_t R, nblk, S, k;
+    int32_t R, nblk, S, k;       // nblk: replica blocks of this launch
+    int32_t blk_base;            // first replica block of this launch (multi-spin-coded kernels)
     uint32_t key0, key1;
-    int4 *best_rec;              // [nblk] (E, step, sweep, slot) per replica block
+    int4 *best_rec;              // [all blocks] (E, step, sweep, slot) per replica block
     int8_t *best_cfg;            // [nblk][np] configuration of that record
     unsigned long long *accepts; // [K] accepted flips per step
     int32_t *sweep_emin;         // [K][S] minimum energy per sweep end
