@@ -176,7 +176,7 @@ def run_reference(args, rank, world):
 # captures summarised in profiles/ (sweep_packed_g63like.md,
 # sweep_msc_g63like.md); reported only when the same kernel runs.
 SWEEP_TRAFFIC = {("k_sweep_packed", 128): 334.719744e6 + 289.454080e6,
-                 ("k_sweep_msc", 256): 112.629504e6 + 55.572736e6}
+                 ("k_sweep_msc+pair", 256): 100.054016e6 + 45.181696e6 + 12.586496e6 + 0.0}
 OPS_PER_ATTEMPT = 20.0   # a quarter Philox4x32-10 block (15) + decision (4) + flip updates (~1)
 INT_LANES_PER_SM = 128   # ALU pipe (LOP3/IADD3) 64 + FMA pipe (IMAD) 64
 
@@ -249,6 +249,11 @@ def run_ours(args, rank, world, dist):
     variant_run = ann.stats()["variant"]
     if variant_run == 1:
         layout, kernel = "multi-spin coded (32 replicas per 32-bit word)", ("k_sweep_msc", args.threads or 256)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        words = (R + 31) // 32
+        if words > sms and words % sms:
+            layout += f"; {words // sms * sms} words in one-CTA blocks + {words % sms} in CTA pairs, concurrently"
+            kernel = ("k_sweep_msc+pair", args.threads or 256)
     elif variant_run == 3:
         layout = "multi-spin coded, a cluster of two CTAs per 32-replica word"
         kernel = ("k_sweep_msc_pair", 256)

@@ -501,25 +501,18 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     pa_default_opts(&o);
     if (opts) o = *opts;
     if (o.variant == PA_VARIANT_AUTO) {
-        // Multi-spin coding is fastest once its 32-replica blocks fill the GPU
-        // (two per SM); otherwise the 4-replica layouts give more blocks. With
-        // few, large colour classes (tori: two) the per-class cluster barrier
-        // is cheap and the CTA-pair kernel's finer work unit wins (measured:
-        // 100x100 torus, R = 32768: 595 vs 516 G attempts/s); with many small
-        // classes (G63-shaped: nine) the single-CTA kernel is as fast or faster.
+        // Multi-spin coding is fastest once its 32-replica words give every SM
+        // at least one block (the words past the largest SM multiple run in the
+        // CTA-pair kernel, see pa_anneal_begin); below that the 4-replica
+        // layouts give more blocks. Measured (G attempts/s, G63-shaped graph):
+        // R = 4096: packed 309, MSC 220; R = 8192: packed 312, MSC 443.
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms <= 0) sms = 152;
-        const int32_t words = (R + 31) / 32;
         const bool msc_ok = c->maxdeg <= 127 && o.field_bits == 0 &&
                             (o.threads_per_cta == 0 || o.threads_per_cta <= 256);
-        if (msc_ok && c->ncol <= 4 && words >= sms)
-            o.variant = PA_VARIANT_MSC_PAIR;
-        else if (msc_ok && words >= 2 * sms)
-            o.variant = PA_VARIANT_MSC;
-        else
-            o.variant = PA_VARIANT_I8;
+        o.variant = (msc_ok && (R + 31) / 32 >= sms) ? PA_VARIANT_MSC : PA_VARIANT_I8;
     }
     if (o.field_bits == 0) o.field_bits = (c->maxdeg <= 127 && c->packed_ok) ? 7 : 16;
     if (K < 0 || R < 1 || R > 65536 || sweeps < 0 || sweeps >= (1 << 28))
