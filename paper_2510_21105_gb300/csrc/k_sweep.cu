@@ -950,24 +950,26 @@ void *select_kernel(int G, int fb, bool weighted, int threads, int mmax) {
 
 }  // namespace
 
+size_t sweep_smem_bytes(const GraphDev &g, int G, int field_bits, int threads) {
+    if (field_bits == 1 || field_bits == 2)   // multi-spin coded: 32 replicas per word (2: CTA pairs)
+        return (size_t)g.np * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + (32 + 32 + 8) * 4;
+    if (field_bits == 7)
+        return (size_t)(g.np + 32) * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + 16 * 4 +
+               (size_t)((((g.np + 31) / 32) + 1) & ~1) * 4 + (size_t)(threads / 32) * PK_QCAP * 8;
+    const int HW = field_bits == 16 ? 2 : 1;
+    return (size_t)g.np * G * 4 * (1 + HW) + (size_t)((g.mmax + 1 + 3) & ~3) * 4 +
+           (size_t)((g.ncol + 1 + 3) & ~3) * 4 + (size_t)(8 * G + 8) * 4;
+}
+
 cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int threads,
                             bool weighted, SweepConfig *cfg) {
-    size_t smem;
-    if (field_bits == 1 || field_bits == 2) {   // multi-spin coded: 32 replicas per word (2: CTA pairs)
+    if (field_bits == 1 || field_bits == 2) {
         G = 8;
         threads = 256;
-        smem = (size_t)g.np * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + (32 + 32 + 8) * 4;
     } else if (field_bits == 7) {
         G = 1;
-        smem = (size_t)(g.np + 32) * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + 16 * 4 +
-               (size_t)((((g.np + 31) / 32) + 1) & ~1) * 4 + (size_t)(threads / 32) * PK_QCAP * 8;
-    } else {
-        const int HW = field_bits == 16 ? 2 : 1;
-        smem = (size_t)g.np * G * 4 * (1 + HW);
-        smem += (size_t)((g.mmax + 1 + 3) & ~3) * 4;
-        smem += (size_t)((g.ncol + 1 + 3) & ~3) * 4;
-        smem += (size_t)(8 * G + 8) * 4;
     }
+    const size_t smem = sweep_smem_bytes(g, G, field_bits, threads);
     void *fn = select_kernel(G, field_bits, weighted, threads, g.mmax);
     // The attribute belongs to the kernel function, not to a context: only ever
     // raise it, so that contexts configured earlier keep launching.

@@ -500,21 +500,48 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     pa_anneal_opts o;
     pa_default_opts(&o);
     if (opts) o = *opts;
+    // Every layout keeps a replica block in shared memory, so the graph size
+    // decides which layouts exist: multi-spin coding needs 4 bytes per vertex
+    // (n up to about 57,000 on GB300), the packed byte 4 bytes per vertex and
+    // n <= 32720, the int16 layout 12 bytes per vertex (n up to about 19,000).
+    int dev = 0, sms = 0, smem_max = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (sms <= 0) sms = 152;
+    if (smem_max <= 0) smem_max = 227 * 1024;
+    const pa::GraphDev gd = c->gdev();
+    auto fits = [&](int fb, int G, int th) { return pa::sweep_smem_bytes(gd, G, fb, th) <= (size_t)smem_max; };
+    const bool msc_fits = c->maxdeg <= 127 && fits(1, 8, 256);
+    const bool packed_fits = c->maxdeg <= 127 && c->packed_ok && fits(7, 1, o.threads_per_cta ? o.threads_per_cta : 128);
+    const bool int16_fits = fits(16, o.replicas_per_cta == 8 ? 2 : 1, 512);
     if (o.variant == PA_VARIANT_AUTO) {
         // Multi-spin coding is fastest once its 32-replica words give every SM
         // at least one block (the words past the largest SM multiple run in the
-        // CTA-pair kernel, see pa_anneal_begin); below that the 4-replica
-        // layouts give more blocks. Measured (G attempts/s, G63-shaped graph):
-        // R = 4096: packed 309, MSC 220; R = 8192: packed 312, MSC 443.
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 152;
-        const bool msc_ok = c->maxdeg <= 127 && o.field_bits == 0 &&
-                            (o.threads_per_cta == 0 || o.threads_per_cta <= 256);
-        o.variant = (msc_ok && (R + 31) / 32 >= sms) ? PA_VARIANT_MSC : PA_VARIANT_I8;
+        // CTA-pair kernel, see below); below that the 4-replica layouts give
+        // more blocks. Measured (G attempts/s, G63-shaped graph): R = 4096:
+        // packed 309, MSC 220; R = 8192: packed 312, MSC 443.
+        const bool msc_ok = msc_fits && o.field_bits == 0 && (o.threads_per_cta == 0 || o.threads_per_cta <= 256);
+        if (msc_ok && (R + 31) / 32 >= sms)
+            o.variant = PA_VARIANT_MSC;
+        else if ((o.field_bits == 0 || o.field_bits == 7) && packed_fits)
+            o.variant = PA_VARIANT_I8;
+        else if (o.field_bits == 0 && !int16_fits && msc_ok)
+            o.variant = PA_VARIANT_MSC;   // the only layout that fits the graph
+        else
+            o.variant = PA_VARIANT_I8;
     }
     if (o.field_bits == 0) o.field_bits = (c->maxdeg <= 127 && c->packed_ok) ? 7 : 16;
+    {
+        const bool msc = o.variant == PA_VARIANT_MSC || o.variant == PA_VARIANT_MSC_PAIR;
+        const int fb = msc ? 1 : o.field_bits;
+        const int G = msc ? 8 : (o.replicas_per_cta == 8 ? 2 : 1);
+        const int th = o.threads_per_cta ? o.threads_per_cta : (msc ? 256 : (o.field_bits == 7 ? 128 : 512));
+        const size_t need = pa::sweep_smem_bytes(gd, G, fb, th);
+        if (need > (size_t)smem_max)
+            return fail(c, PA_EINVAL, "graph too large for this layout: a sweep block needs " + std::to_string(need) +
+                                          " bytes of shared memory, the device allows " + std::to_string(smem_max));
+    }
     if (K < 0 || R < 1 || R > 65536 || sweeps < 0 || sweeps >= (1 << 28))
         return fail(c, PA_EINVAL, "K, R (1..65536) or sweeps out of range");
     if (int rc = validate_opts(c, o)) return rc;

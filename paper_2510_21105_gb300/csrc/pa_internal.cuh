@@ -127,6 +127,9 @@ struct SweepConfig {
     int grid;
     size_t smem;
 };
+// Dynamic shared memory of one sweep CTA (G: 4-replica groups of the int8/int16 layouts;
+// field_bits 1/2 multi-spin coded, 7 packed, 8/16 int8/int16 fields).
+size_t sweep_smem_bytes(const GraphDev &g, int G, int field_bits, int threads);
 cudaError_t sweep_configure(const GraphDev &g, int R, int G, int field_bits, int threads,
                             bool weighted, SweepConfig *cfg);
 cudaError_t launch_sweep(const SweepConfig &cfg, const SweepArgs &a, cudaStream_t st);

@@ -264,3 +264,41 @@ def test_parity_msc_many_words_ragged_last_word(variant):
     gpu = run_gpu(g, betas, 4937, 2, seed=31, variant=variant, nlm_period=2)
     orc = run_oracle(g, betas, 4937, 2, seed=31, nlm_period=2)
     assert_parity(gpu, orc, g, 4937, 2)
+
+
+def test_parity_largest_graph_that_fits_shared_memory():
+    """n = 40000: too large for the packed (n <= 32720) and int16 layouts, so
+    AUTO falls back to multi-spin coding even with fewer words than SMs; block
+    moves run at this size (Houdayer moves need n <= 32768 and are refused)."""
+    g = wl.gnm(40000, 60000, seed=61)
+    betas = wl.linear_betas(0.2, 1.5, 3)
+    gpu = run_gpu(g, betas, 40, 1, seed=3, nlm_period=2, nlm_kind=1, nlm_block=8)
+    assert gpu["stats"]["variant"] == 1
+    orc = run_oracle(g, betas, 40, 1, seed=3, nlm_period=2, nlm_kind=1, nlm_block=8)
+    assert_parity(gpu, orc, g, 40, 1)
+    a = B.Annealer.from_graph(g)
+    with pytest.raises(B.PaError) as e:
+        a.begin(betas, R=40, S=1, seed=3, nlm_period=2)
+    assert e.value.code == B.PA_EINVAL
+    a.close()
+
+
+def test_layouts_that_do_not_fit_are_refused():
+    """Graphs whose replica block exceeds the per-CTA shared memory are
+    rejected with PA_EINVAL, not launched."""
+    require_gpu()
+    big = wl.gnm(60000, 60000, seed=62)       # 240 KB per multi-spin-coded block
+    a = B.Annealer.from_graph(big)
+    with pytest.raises(B.PaError) as e:
+        a.begin(wl.linear_betas(0.2, 1.5, 2), R=64, S=1, seed=1)
+    assert e.value.code == B.PA_EINVAL and "shared memory" in str(e.value)
+    a.close()
+    mid = wl.gnm(20000, 40000, seed=63)       # int16 layout: 240 KB; packed fits
+    a = B.Annealer.from_graph(mid)
+    with pytest.raises(B.PaError) as e:
+        a.begin(wl.linear_betas(0.2, 1.5, 2), R=64, S=1, seed=1, field_bits=16)
+    assert e.value.code == B.PA_EINVAL
+    a.begin(wl.linear_betas(0.2, 1.5, 2), R=64, S=1, seed=1)
+    a.run(2)
+    a.sync()
+    a.close()
