@@ -103,3 +103,14 @@ def test_full_g63like_anneal_properties():
     assert np.all(rec["T"] > 0)
     # a G63-shaped random graph: the cut should be far above the random-cut value M/2
     assert cut > 0.62 * g.m
+
+
+def test_replay_maximum_replica_count():
+    """R = 65536, the largest population the ABI takes: 2048 words, 1976 in
+    one-CTA blocks and 72 in CTA pairs; copy counts of all slots and the
+    spins of sampled slots replayed by the oracle at step 2."""
+    c = wl.CONFIGS["g63like"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    subset = np.array([0, 31, 32, 4096, 63231, 63232, 65535])
+    _replay_check(g, betas, 65536, 2, c["seed"], 2, subset)
