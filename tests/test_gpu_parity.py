@@ -200,6 +200,29 @@ def test_degenerate_cases():
     a.close()
 
 
+@pytest.mark.parametrize("variant,field_bits", [(0, 16), (0, 8), (0, 7), (1, 0), (3, 0)],
+                         ids=["int16", "int8", "packed", "msc", "msc-pair"])
+def test_degenerate_cases_every_layout(variant, field_bits):
+    """Degenerate inputs in every layout, element by element against the oracle:
+    a single vertex, an edgeless graph (every attempt has m = 0 and is accepted),
+    one replica (plain simulated annealing: resampling is the identity), a
+    single temperature step, and beta = 0 throughout (uniform acceptance)."""
+    kw = dict(variant=variant, field_bits=field_bits)
+    cases = [
+        (wl.from_edges(1, [], []), wl.linear_betas(0.5, 1.0, 3), 5, 2),
+        (wl.from_edges(50, [], []), wl.linear_betas(0.5, 1.0, 3), 33, 2),
+        (wl.gnp(60, 0.1, seed=71), wl.linear_betas(0.1, 2.0, 6), 1, 3),
+        (wl.torus(6, seed=72), np.array([0.7]), 40, 4),
+        (wl.gnp(60, 0.1, seed=73), np.zeros(4), 36, 2),
+    ]
+    for g, betas, R, S in cases:
+        gpu = run_gpu(g, betas, R, S, seed=5, **kw)
+        orc = run_oracle(g, betas, R, S, seed=5)
+        assert_parity(gpu, orc, g, R, S)
+        if R == 1:
+            assert np.all(orc.step_counts == 1)
+
+
 @pytest.mark.parametrize("kw,K,split", [
     (dict(nlm_period=4), 10, 6),
     (dict(variant=1), 10, 3),
