@@ -392,6 +392,13 @@ def run_batch(args):
     ev1.record()
     torch.cuda.synchronize()
     plain_ms = ev0.elapsed_time(ev1)
+    # plain with the library's default layout choice (no per-instance tuning)
+    ev0.record()
+    for ann, it in zip(anns, inst):
+        ann.anneal(betas, it["R"], S, it["seed"])
+    ev1.record()
+    torch.cuda.synchronize()
+    plain_default_ms = ev0.elapsed_time(ev1)
     items = [(ann, betas, it["R"], S, it["seed"], K, o) for ann, it, o in zip(anns, inst, opts_b)]
     B.pa_batch_anneal(items, n_streams=args.streams, use_graph=True)   # warm-up (and graph build)
     times = [B.pa_batch_anneal(items, n_streams=args.streams, use_graph=True) for _ in range(max(args.steps, 1))]
@@ -402,6 +409,8 @@ def run_batch(args):
     line = {"mode": "batch", "metric": "batched attempts/s (64 mixed instances) vs plain one-instance-per-launch",
             "value": attempts / (batch_ms / 1e3), "unit": UNIT, "plain_value": attempts / (plain_ms / 1e3),
             "ratio": plain_ms / batch_ms, "batch_ms": batch_ms, "plain_ms": plain_ms,
+            "plain_default_value": attempts / (plain_default_ms / 1e3), "plain_default_ms": plain_default_ms,
+            "ratio_vs_default_plain": plain_default_ms / batch_ms,
             "bit_identical_to_plain": same, "instances": len(inst), "attempts": attempts,
             "autotune_s": tune_s,
             "layouts_plain": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts)),
