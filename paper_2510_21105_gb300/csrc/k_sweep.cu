@@ -607,13 +607,46 @@ __device__ __forceinline__ uint4 philox_from_shared(const PhiloxShared &p, uint3
     return c;
 }
 
+// Energy bookkeeping of the multi-spin-coded kernels. With |m| <= 31
+// (NPL <= 5) every item adds, per replica 4g + q, 32 + m for an accepted flip
+// and 32 for a rejected attempt into byte q of the lane's word ebias[g]; four
+// items stay below 256 in every byte. After at most four items per lane the
+// warp flushes: the 16-bit halves of the words are summed over the 32 lanes
+// (at most 32 * 252 < 2^16, so no half carries into the next), the bias of 32
+// per item is removed and lane r adds twice the result, the energy change of
+// replica r, to Eacc[r]. This replaces one divergent shared atomic per accepted
+// flip by branch-free byte arithmetic; the sums are exact integers, so the
+// energies are the same as with per-flip updates. Wider counters (|m| up to
+// 127) keep the per-flip atomics.
+template <int NPL>
+struct MscPackedE {
+    static constexpr bool value = NPL <= 5;
+};
+
+__device__ __forceinline__ void msc_flush_energy(uint32_t (&ebias)[8], int &cnt, int32_t *Eacc, int lane) {
+    const int nwarp = (int)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)cnt);
+    uint32_t mine = 0;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        const uint32_t slo = __reduce_add_sync(0xFFFFFFFFu, ebias[g] & 0x00FF00FFu);          // bytes 0, 2
+        const uint32_t shi = __reduce_add_sync(0xFFFFFFFFu, (ebias[g] >> 8) & 0x00FF00FFu);   // bytes 1, 3
+        if ((lane >> 2) == g) mine = (lane & 1) ? shi : slo;
+        ebias[g] = 0u;
+    }
+    const int dm = (int)((lane & 2) ? (mine >> 16) : (mine & 0xFFFFu)) - 32 * nwarp;
+    if (dm) atomicAdd(&Eacc[lane], 2 * dm);
+    cnt = 0;
+}
+
 // One (position, word) item of a multi-spin-coded sweep: counts the frustrated
-// bonds of the 32 replicas, decides the 32 attempts and adds the energy change
-// of every accepted flip to Eacc (local or a cluster peer's shared memory).
-// Returns the mask of accepted replicas.
+// bonds of the 32 replicas, decides the 32 attempts and records the energy
+// change of every accepted flip, either in the lane's packed counters ebias
+// (MscPackedE) or by a shared atomic on Eacc (local or a cluster peer's shared
+// memory). Returns the mask of accepted replicas.
 template <int NPL, bool WEIGHTED>
 __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t *Wsm, const uint32_t *T256, int p,
-                                             uint32_t x, uint32_t c3, int blk, int32_t *Eacc) {
+                                             uint32_t x, uint32_t c3, int blk, int32_t *Eacc,
+                                             uint32_t (&ebias)[8]) {
     const uint32_t e0 = __ldg(&a.g.rp[p]), e1 = __ldg(&a.g.rp[p + 1]);
     const uint32_t vid = __ldg(&a.g.vid[p]);
     uint32_t pl[NPL];
@@ -650,7 +683,10 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
             ag |= (uint32_t)((idx <= 128u) | (uu[q] < T256[idx])) << (8 * q);
         }
         acc32 |= ag << g;
-        if (ag) {   // energy change 2m = 2(mb byte - 128) of each accepted replica
+        if (MscPackedE<NPL>::value) {   // byte q: accepted ? 32 + m : 32 (mb byte = 128 + m >= 97)
+            const uint32_t A = ag * 0xFFu;
+            ebias[g] += ((mb - 0x60606060u) & A) | (0x20202020u & ~A);
+        } else if (ag) {   // energy change 2m = 2(mb byte - 128) of each accepted replica
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if ((ag >> (8 * q)) & 1u) atomicAdd(&Eacc[4 * g + q], 2 * ((int)((mb >> (8 * q)) & 0xFFu) - 128));
@@ -707,17 +743,26 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
         uint32_t vmask = 0u;   // bits of the live replicas
         for (int r = 0; r < 32; ++r) vmask |= (slot0 + r < a.R ? 1u : 0u) << msc_bit(r);
         uint32_t nacc = 0;
+        uint32_t ebias[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        int cnt = 0;
         for (int s = 0; s < nsweeps; ++s) {
             const uint32_t c3 = TAG_SWEEP | (uint32_t)s;
             for (int c = 0; c < a.g.ncol; ++c) {
-                const int p1 = cls[c + 1];
-                for (int p = cls[c] + tid; p < p1; p += NT) {
-                    const uint32_t x = Wsm[p];
-                    const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, Eacc);
-                    if (acc32) {
-                        Wsm[p] = x ^ acc32;
-                        nacc += __popc(acc32 & vmask);
+                const int p0 = cls[c], p1 = cls[c + 1];
+                const int nr = (p1 - p0 + NT - 1) / NT;   // rounds of the class, uniform over the CTA
+                for (int rd = 0; rd < nr; ++rd) {
+                    const int p = p0 + tid + rd * NT;
+                    if (p < p1) {
+                        const uint32_t x = Wsm[p];
+                        const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, Eacc, ebias);
+                        if (acc32) {
+                            Wsm[p] = x ^ acc32;
+                            nacc += __popc(acc32 & vmask);
+                        }
+                        ++cnt;
                     }
+                    if (MscPackedE<NPL>::value && ((rd & 3) == 3 || rd == nr - 1))
+                        msc_flush_energy(ebias, cnt, Eacc, lane);
                 }
                 __syncthreads();
             }
@@ -833,18 +878,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
         uint32_t vmask = 0u;   // bits of the live replicas
         for (int r = 0; r < 32; ++r) vmask |= (slot0 + r < a.R ? 1u : 0u) << msc_bit(r);
         uint32_t nacc = 0;
+        uint32_t ebias[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        int cnt = 0;
         for (int s = 0; s < nsweeps; ++s) {
             const uint32_t c3 = TAG_SWEEP | (uint32_t)s;
             for (int c = 0; c < a.g.ncol; ++c) {
-                const int p1 = cls[c + 1];
-                for (int p = cls[c] + 2 * tid + rank; p < p1; p += 2 * NT) {
-                    const uint32_t x = Wsm[p];
-                    const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, E0);
-                    if (acc32) {
-                        Wsm[p] = x ^ acc32;
-                        Wpeer[p] = x ^ acc32;
-                        nacc += __popc(acc32 & vmask);
+                const int p0 = cls[c], p1 = cls[c + 1];
+                const int nr = (p1 - p0 + 2 * NT - 1) / (2 * NT);   // rounds, uniform over the cluster
+                for (int rd = 0; rd < nr; ++rd) {
+                    const int p = p0 + 2 * tid + rank + rd * 2 * NT;
+                    if (p < p1) {
+                        const uint32_t x = Wsm[p];
+                        const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, E0, ebias);
+                        if (acc32) {
+                            Wsm[p] = x ^ acc32;
+                            Wpeer[p] = x ^ acc32;
+                            nacc += __popc(acc32 & vmask);
+                        }
+                        ++cnt;
                     }
+                    if (MscPackedE<NPL>::value && ((rd & 3) == 3 || rd == nr - 1))
+                        msc_flush_energy(ebias, cnt, E0, lane);
                 }
                 cluster.sync();
             }
