@@ -550,10 +550,15 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
 // group's four replicas are one bit of each byte. No fields are kept:
 // an item (p, word) XORs its word with each neighbour's word (and with all
 // ones for a -1 weight), so bit r of d_j is 1 iff the bond (p, j) contributes
-// +1 to m_r = -x_p h_p; a bit-sliced counter over the neighbours gives c_r and
-// m_r = 2 c_r - deg(p). Groups of four replicas are spread to bytes and
-// decided exactly like the packed layout (same thresholds, same Philox word
-// (vertex, slot/4, step, sweep)). Accepted replicas flip with one XOR.
+// +1 to m_r = -x_p h_p; a bit-sliced counter over the neighbours (carry-save
+// adders, four bonds per step) gives c_r and m_r = 2 c_r - deg(p). An 8 x 8
+// bit transpose in every byte lane turns the counter planes into one byte per
+// replica, group by group, and each group is decided exactly like the packed
+// layout (same thresholds, same Philox word (vertex, slot/4, step, sweep)).
+// With |m| <= 31 the byte holds 4m + 128, which is also the byte offset of
+// the threshold of m in a table kept at the start of shared memory (entry
+// m + 32), so the lookup needs no address arithmetic. Accepted replicas flip
+// with one XOR.
 __device__ __forceinline__ int msc_bit(int r) {   // bit of replica r = 4g + q in a word
     return 8 * (r & 3) + (r >> 2);
 }
@@ -652,7 +657,34 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
     uint32_t pl[NPL];
 #pragma unroll
     for (int b = 0; b < NPL; ++b) pl[b] = 0u;
-    for (uint32_t e = e0; e < e1; ++e) {
+    uint32_t e = e0;
+    for (; e + 4 <= e1; e += 4) {   // four bonds per step through carry-save adders
+        uint32_t w0 = Wsm[__ldg(&a.g.col[e])], w1 = Wsm[__ldg(&a.g.col[e + 1])];
+        uint32_t w2 = Wsm[__ldg(&a.g.col[e + 2])], w3 = Wsm[__ldg(&a.g.col[e + 3])];
+        if (WEIGHTED) {
+            if (__ldg(&a.g.wt[e]) < 0) w0 = ~w0;
+            if (__ldg(&a.g.wt[e + 1]) < 0) w1 = ~w1;
+            if (__ldg(&a.g.wt[e + 2]) < 0) w2 = ~w2;
+            if (__ldg(&a.g.wt[e + 3]) < 0) w3 = ~w3;
+        }
+        const uint32_t s01 = w0 ^ w1, c01 = (x ^ w0) & (x ^ w1);   // d0 + d1 = s01 + 2 c01
+        const uint32_t s23 = w2 ^ w3, c23 = (x ^ w2) & (x ^ w3);
+        const uint32_t s = s01 ^ s23, cs = s01 & s23;              // d0 + .. + d3 = s + 2 (c01 + c23 + cs)
+        const uint32_t t = pl[0] & s;
+        pl[0] ^= s;
+        const uint32_t u1 = pl[1] ^ c01 ^ c23, k1 = (pl[1] & c01) | (c23 & (pl[1] | c01));
+        const uint32_t k2 = (u1 & cs) | (t & (u1 | cs));
+        pl[1] = u1 ^ cs ^ t;
+        uint32_t k = (pl[2] & k1) | (k2 & (pl[2] | k1));
+        pl[2] ^= k1 ^ k2;
+#pragma unroll
+        for (int b = 3; b < NPL; ++b) {
+            const uint32_t carry = pl[b] & k;
+            pl[b] ^= k;
+            k = carry;
+        }
+    }
+    for (; e < e1; ++e) {
         uint32_t d = x ^ Wsm[__ldg(&a.g.col[e])];
         if (WEIGHTED && __ldg(&a.g.wt[e]) < 0) d = ~d;
 #pragma unroll
@@ -663,29 +695,49 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
         }
     }
     const uint32_t deg = e1 - e0;
-    const uint32_t base = 128u - deg;   // mb = 2c + 128 - deg
+    constexpr bool PK = MscPackedE<NPL>::value;
+    const uint32_t base = PK ? 128u - 4u * deg : 128u - deg;   // mb byte = 4m + 128 (PK, deg <= 31) or m + 128
     const PhiloxShared ps = philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1);
+    // Byte q of r[g] = c of replica 4g + q: an 8 x 8 bit transpose in every byte lane.
+    uint32_t r[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) r[b] = b < NPL ? pl[b] : 0u;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const uint32_t t = ((r[b] >> 4) ^ r[b + 4]) & 0x0F0F0F0Fu;
+        r[b] ^= t << 4;
+        r[b + 4] ^= t;
+    }
+#pragma unroll
+    for (int b = 0; b < 8; b += (b & 1) ? 3 : 1) {   // 0, 1, 4, 5
+        const uint32_t t = ((r[b] >> 2) ^ r[b + 2]) & 0x33333333u;
+        r[b] ^= t << 2;
+        r[b + 2] ^= t;
+    }
+#pragma unroll
+    for (int b = 0; b < 8; b += 2) {
+        const uint32_t t = ((r[b] >> 1) ^ r[b + 1]) & 0x55555555u;
+        r[b] ^= t << 1;
+        r[b + 1] ^= t;
+    }
     uint32_t acc32 = 0;
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
-        // Byte q of 2c for group g: bit 8q + g of plane b rotated to bit 8q + b + 1.
-        uint32_t c2 = 0;
-#pragma unroll
-        for (int b = 0; b < NPL; ++b)
-            c2 |= __funnelshift_r(pl[b], pl[b], (uint32_t)(g - b - 1) & 31u) & (0x02020202u << b);
-        const uint32_t mb = c2 + base * 0x01010101u;
+        const uint32_t mb = r[g] * (PK ? 8u : 2u) + base * 0x01010101u;
         const uint4 u = philox_from_shared(ps, (uint32_t)(blk * 8 + g), a.key0, a.key1);
         const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
         uint32_t ag = 0;   // acceptances of the group, one bit per byte
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
-            ag |= (uint32_t)((idx <= 128u) | (uu[q] < T256[idx])) << (8 * q);
+            const uint32_t thr = PK ? *reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(T256) + idx)
+                                    : T256[idx];
+            ag |= (uint32_t)((idx <= 128u) | (uu[q] < thr)) << (8 * q);
         }
         acc32 |= ag << g;
-        if (MscPackedE<NPL>::value) {   // byte q: accepted ? 32 + m : 32 (mb byte = 128 + m >= 97)
+        if (PK) {   // byte q: accepted ? 32 + m : 32, with m + 32 = (mb byte) / 4
             const uint32_t A = ag * 0xFFu;
-            ebias[g] += ((mb - 0x60606060u) & A) | (0x20202020u & ~A);
+            ebias[g] += ((mb >> 2) & 0x3F3F3F3Fu & A) | (0x20202020u & ~A);
         } else if (ag) {   // energy change 2m = 2(mb byte - 128) of each accepted replica
 #pragma unroll
             for (int q = 0; q < 4; ++q)
@@ -701,9 +753,9 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     const bool act = !a.active || a.active[a.k];
     const int nsweeps = act ? a.S : 0;
     const int np = a.g.np, n = a.g.n;
-    uint32_t *Wsm = reinterpret_cast<uint32_t *>(smem);           // [np]
-    uint32_t *T256 = Wsm + np;                                      // [256] by m + 128
-    int32_t *cls = reinterpret_cast<int32_t *>(T256 + 256);
+    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] thresholds by m + 32 (|m| <= 31) or m + 128
+    uint32_t *Wsm = T256 + 256;                                     // [np]
+    int32_t *cls = reinterpret_cast<int32_t *>(Wsm + np);
     const int csz = (a.g.ncol + 1 + 3) & ~3;
     int32_t *Eacc = cls + csz;      // [32]
     int32_t *PS = Eacc + 32;        // [32]
@@ -712,7 +764,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
     for (int i = tid; i < 256; i += NT) {
-        const int m = i - 128;
+        const int m = i - (MscPackedE<NPL>::value ? 32 : 128);
         T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
     }
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
@@ -834,9 +886,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
     const bool act = !a.active || a.active[a.k];
     const int nsweeps = act ? a.S : 0;
     const int np = a.g.np, n = a.g.n;
-    uint32_t *Wsm = reinterpret_cast<uint32_t *>(smem);           // [np]
-    uint32_t *T256 = Wsm + np;                                      // [256] by m + 128
-    int32_t *cls = reinterpret_cast<int32_t *>(T256 + 256);
+    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] thresholds by m + 32 (|m| <= 31) or m + 128
+    uint32_t *Wsm = T256 + 256;                                     // [np]
+    int32_t *cls = reinterpret_cast<int32_t *>(Wsm + np);
     const int csz = (a.g.ncol + 1 + 3) & ~3;
     int32_t *Eacc = cls + csz;      // [32] (used in CTA 0)
     int32_t *PS = Eacc + 32;        // [32]
@@ -847,7 +899,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
     for (int i = tid; i < 256; i += NT) {
-        const int m = i - 128;
+        const int m = i - (MscPackedE<NPL>::value ? 32 : 128);
         T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
     }
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
