@@ -556,9 +556,12 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
 // replica, group by group, and each group is decided exactly like the packed
 // layout (same thresholds, same Philox word (vertex, slot/4, step, sweep)).
 // With |m| <= 31 the byte holds 4m + 128, which is also the byte offset of
-// the threshold of m in a table kept at the start of shared memory (entry
-// m + 32), so the lookup needs no address arithmetic. Accepted replicas flip
-// with one XOR.
+// the entry of m in a table kept at the start of shared memory, so the lookup
+// needs no address arithmetic. The entry is 2^64 - T[m] split into a low word
+// (offset 4m + 128) and a high word (256 bytes further), with T = 2^32 for
+// m <= 0 (always accepted) and 0 kept as 0 (never accepted): the high word of
+// u + entry is all ones exactly when u < T[m], so one 64-bit add decides an
+// attempt, the m <= 0 rule included. Accepted replicas flip with one XOR.
 __device__ __forceinline__ int msc_bit(int r) {   // bit of replica r = 4g + q in a word
     return 8 * (r & 3) + (r >> 2);
 }
@@ -721,24 +724,33 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
         r[b + 1] ^= t;
     }
     uint32_t acc32 = 0;
+    const uint32_t mq0 = (32u - deg) * 0x01010101u;   // 2c + 32 - deg = m + 32 per byte (PK)
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
         const uint32_t mb = r[g] * (PK ? 8u : 2u) + base * 0x01010101u;
         const uint4 u = philox_from_shared(ps, (uint32_t)(blk * 8 + g), a.key0, a.key1);
         const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
         uint32_t ag = 0;   // acceptances of the group, one bit per byte
+        if (PK) {
+            uint32_t acc[4];   // all ones iff accepted: high word of u + (2^64 - threshold)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
-            const uint32_t thr = PK ? *reinterpret_cast<const uint32_t *>(reinterpret_cast<const unsigned char *>(T256) + idx)
-                                    : T256[idx];
-            ag |= (uint32_t)((idx <= 128u) | (uu[q] < thr)) << (8 * q);
+            for (int q = 0; q < 4; ++q) {
+                const unsigned char *tb = reinterpret_cast<const unsigned char *>(T256) + ((mb >> (8 * q)) & 0xFFu);
+                const uint32_t lo = *reinterpret_cast<const uint32_t *>(tb), hi = *reinterpret_cast<const uint32_t *>(tb + 256);
+                acc[q] = (uint32_t)(((unsigned long long)uu[q] + (((unsigned long long)hi << 32) | lo)) >> 32);
+            }
+            const uint32_t A = __byte_perm(__byte_perm(acc[0], acc[1], 0x0040u), __byte_perm(acc[2], acc[3], 0x0040u), 0x5410u);
+            ag = A & 0x01010101u;
+            ebias[g] += ((r[g] * 2u + mq0) & A) | (0x20202020u & ~A);   // byte q: accepted ? 32 + m : 32
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
+                ag |= (uint32_t)((idx <= 128u) | (uu[q] < T256[idx])) << (8 * q);
+            }
         }
         acc32 |= ag << g;
-        if (PK) {   // byte q: accepted ? 32 + m : 32, with m + 32 = (mb byte) / 4
-            const uint32_t A = ag * 0xFFu;
-            ebias[g] += ((mb >> 2) & 0x3F3F3F3Fu & A) | (0x20202020u & ~A);
-        } else if (ag) {   // energy change 2m = 2(mb byte - 128) of each accepted replica
+        if (!PK && ag) {   // energy change 2m = 2(mb byte - 128) of each accepted replica
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if ((ag >> (8 * q)) & 1u) atomicAdd(&Eacc[4 * g + q], 2 * ((int)((mb >> (8 * q)) & 0xFFu) - 128));
@@ -753,7 +765,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     const bool act = !a.active || a.active[a.k];
     const int nsweeps = act ? a.S : 0;
     const int np = a.g.np, n = a.g.n;
-    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] thresholds by m + 32 (|m| <= 31) or m + 128
+    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] decision table (see above) or thresholds by m + 128
     uint32_t *Wsm = T256 + 256;                                     // [np]
     int32_t *cls = reinterpret_cast<int32_t *>(Wsm + np);
     const int csz = (a.g.ncol + 1 + 3) & ~3;
@@ -764,8 +776,16 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
     for (int i = tid; i < 256; i += NT) {
-        const int m = i - (MscPackedE<NPL>::value ? 32 : 128);
-        T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
+        if (MscPackedE<NPL>::value) {
+            // words 0..63: low halves of 2^64 - threshold of m = i - 32; words 64..127: high halves
+            const int m = (i & 63) - 32;
+            const uint32_t thr = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
+            const bool always = m <= 0, never = !always && thr == 0u;
+            T256[i] = i < 64 ? ((always || never) ? 0u : 0u - thr) : (i < 128 && !never ? 0xFFFFFFFFu : 0u);
+        } else {
+            const int m = i - 128;
+            T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
+        }
     }
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
 
@@ -886,7 +906,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
     const bool act = !a.active || a.active[a.k];
     const int nsweeps = act ? a.S : 0;
     const int np = a.g.np, n = a.g.n;
-    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] thresholds by m + 32 (|m| <= 31) or m + 128
+    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] decision table (see above) or thresholds by m + 128
     uint32_t *Wsm = T256 + 256;                                     // [np]
     int32_t *cls = reinterpret_cast<int32_t *>(Wsm + np);
     const int csz = (a.g.ncol + 1 + 3) & ~3;
@@ -899,8 +919,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
     for (int i = tid; i < 256; i += NT) {
-        const int m = i - (MscPackedE<NPL>::value ? 32 : 128);
-        T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
+        if (MscPackedE<NPL>::value) {
+            // words 0..63: low halves of 2^64 - threshold of m = i - 32; words 64..127: high halves
+            const int m = (i & 63) - 32;
+            const uint32_t thr = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
+            const bool always = m <= 0, never = !always && thr == 0u;
+            T256[i] = i < 64 ? ((always || never) ? 0u : 0u - thr) : (i < 128 && !never ? 0xFFFFFFFFu : 0u);
+        } else {
+            const int m = i - 128;
+            T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
+        }
     }
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
 
