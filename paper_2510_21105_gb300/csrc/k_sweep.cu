@@ -740,7 +740,7 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
                 acc[q] = (uint32_t)(((unsigned long long)uu[q] + (((unsigned long long)hi << 32) | lo)) >> 32);
             }
             const uint32_t A = __byte_perm(__byte_perm(acc[0], acc[1], 0x0040u), __byte_perm(acc[2], acc[3], 0x0040u), 0x5410u);
-            ag = A & 0x01010101u;
+            acc32 |= A & (0x01010101u << g);
             ebias[g] += ((r[g] * 2u + mq0) & A) | (0x20202020u & ~A);   // byte q: accepted ? 32 + m : 32
         } else {
 #pragma unroll
@@ -748,8 +748,8 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
                 const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
                 ag |= (uint32_t)((idx <= 128u) | (uu[q] < T256[idx])) << (8 * q);
             }
+            acc32 |= ag << g;
         }
-        acc32 |= ag << g;
         if (!PK && ag) {   // energy change 2m = 2(mb byte - 128) of each accepted replica
 #pragma unroll
             for (int q = 0; q < 4; ++q)
