@@ -518,12 +518,18 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     if (o.variant == PA_VARIANT_AUTO) {
         // Multi-spin coding is fastest once its 32-replica words give every SM
         // at least one block (the words past the largest SM multiple run in the
-        // CTA-pair kernel, see below); below that the 4-replica layouts give
-        // more blocks. Measured (G attempts/s, G63-shaped graph): R = 4096:
-        // packed 309, MSC 220; R = 8192: packed 312, MSC 443.
+        // CTA-pair kernel, see below). With fewer words, down to about 40% of
+        // the SM count, the CTA-pair kernel (two CTAs per word) still beats the
+        // 4-replica packed layout; below that the packed layout's smaller
+        // blocks win. Measured (G attempts/s, packed / MSC / MSC pair):
+        // G63-shaped R = 2048: 251 / 196 / 255; R = 4096: 357 / 388 / 413;
+        // R = 8192: 362 / 558 / 533; torus 100x100 R = 2048: 281 / 265 / 445.
         const bool msc_ok = msc_fits && o.field_bits == 0 && (o.threads_per_cta == 0 || o.threads_per_cta <= 256);
-        if (msc_ok && (R + 31) / 32 >= sms)
+        const int32_t words = (R + 31) / 32;
+        if (msc_ok && words >= sms)
             o.variant = PA_VARIANT_MSC;
+        else if (msc_ok && 5 * words >= 2 * sms)
+            o.variant = PA_VARIANT_MSC_PAIR;
         else if ((o.field_bits == 0 || o.field_bits == 7) && packed_fits)
             o.variant = PA_VARIANT_I8;
         else if (o.field_bits == 0 && !int16_fits && msc_ok)
