@@ -181,7 +181,19 @@ OPS_PER_ATTEMPT = 20.0   # a quarter Philox4x32-10 block (15) + decision (4) + f
 INT_LANES_PER_SM = 128   # ALU pipe (LOP3/IADD3) 64 + FMA pipe (IMAD) 64
 
 
-def sweep_roofline(stats, attempts_per_launch, peaks, kernel):
+def smem_bytes_per_attempt(kernel, mean_degree, accept_rate):
+    """Algorithmic shared-memory bytes of one attempt. Multi-spin coded: per
+    (position, 32-replica word) item the neighbours' words and the item's own
+    word read and written, spread over 32 attempts, plus the two 4-byte halves
+    of the decision-table entry of each attempt. 4-replica layouts: the
+    spin/field byte read and written and the threshold word, plus the
+    neighbours' field bytes read and written on an accepted flip."""
+    if kernel[0].startswith("k_sweep_msc"):
+        return (4.0 * mean_degree + 8.0) / 32.0 + 8.0
+    return 2.0 + 4.0 + accept_rate * 2.0 * mean_degree
+
+
+def sweep_roofline(stats, attempts_per_launch, peaks, kernel, mean_degree, accept_rate):
     """Roofline of the sweep kernel (dominant kernel): integer-issue bound."""
     launches = max(stats["sweep_launches"], 1)
     t = stats["sweep_ms"] / launches / 1e3
@@ -195,7 +207,9 @@ def sweep_roofline(stats, attempts_per_launch, peaks, kernel):
             "kernel": f"{kernel[0]}<{kernel[1]} threads>", "avg_launch_ms": t * 1e3,
             "attempts_per_s_in_kernel": attempts_per_launch / t,
             "peak_source": f"derived: {SMS} SMs x {INT_LANES_PER_SM} integer lanes x {clk:.0f} MHz",
-            "smem_frac": attempts_per_launch * 6.6 / t / (SMS * 128 * clk * 1e6)}
+            "smem_bytes_per_attempt": smem_bytes_per_attempt(kernel, mean_degree, accept_rate),
+            "smem_frac": attempts_per_launch * smem_bytes_per_attempt(kernel, mean_degree, accept_rate) / t
+                         / (SMS * 128 * clk * 1e6)}
 
 
 def max_over_ranks(x: float, dist, device: str = "cpu") -> float:
@@ -287,7 +301,7 @@ def run_ours(args, rank, world, dist):
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = aggregate_value(attempts, world, ms_max)
     clocks = clk.summary()
-    roof = sweep_roofline(stats_acc, g.n * R * S, peaks, kernel)
+    roof = sweep_roofline(stats_acc, g.n * R * S, peaks, kernel, 2.0 * g.m / g.n, acc_rate)
     ann.close()
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the region

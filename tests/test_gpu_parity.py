@@ -325,3 +325,23 @@ def test_layouts_that_do_not_fit_are_refused():
     a.run(2)
     a.sync()
     a.close()
+
+
+@pytest.mark.parametrize("R,expect", [(1903, 0), (2500, 3), (4832, 3), (4865, 1)])
+def test_auto_layout_choice_by_population(R, expect):
+    """The default layout follows the number of 32-replica words against the
+    SM count: packed below 40% of the SMs, the CTA-pair kernel up to one word
+    per SM, then the one-CTA kernel (with its CTA-pair tail). Every choice
+    gives the oracle's results."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    words = (R + 31) // 32
+    want = 1 if words >= sms else (3 if 5 * words >= 2 * sms else 0)
+    if sms == 152:
+        assert want == expect
+    g = wl.gnp(120, 0.1, seed=71)
+    betas = wl.linear_betas(0.3, 2.0, 3)
+    gpu = run_gpu(g, betas, R, 1, seed=5)
+    assert gpu["stats"]["variant"] == want
+    orc = run_oracle(g, betas, R, 1, seed=5)
+    assert_parity(gpu, orc, g, R, 1)
