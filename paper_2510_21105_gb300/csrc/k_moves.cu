@@ -154,7 +154,8 @@ __global__ void k_nlm_pair(NlmArgs a, const int32_t *order) {
     }
     // Fields and energies of both replicas, recomputed.
     long long Ea = 0, Eb = 0;
-    int16_t *fa = a.fields + (size_t)sa * np, *fb = a.fields + (size_t)sb * np;
+    int16_t *fa = a.fields ? a.fields + (size_t)sa * np : nullptr;
+    int16_t *fb = a.fields ? a.fields + (size_t)sb * np : nullptr;
     for (int p = tid; p < np; p += NT) {
         int ha = 0, hb = 0;
         if (p < n) {
@@ -168,8 +169,10 @@ __global__ void k_nlm_pair(NlmArgs a, const int32_t *order) {
             Ea += (long long)xa[p] * ha;
             Eb += (long long)xb[p] * hb;
         }
-        fa[p] = (int16_t)ha;
-        fb[p] = (int16_t)hb;
+        if (a.fields) {   // layouts that keep fields (the multi-spin-coded ones do not)
+            fa[p] = (int16_t)ha;
+            fb[p] = (int16_t)hb;
+        }
     }
     for (int off = 16; off; off >>= 1) {
         Ea += __shfl_xor_sync(0xFFFFFFFFu, Ea, off);
@@ -304,8 +307,8 @@ __global__ void __launch_bounds__(256) k_nlm_block(NlmArgs a) {
         }
     }
     __syncthreads();
-    int16_t *gh = a.fields + (size_t)r * np;
-    for (int p = tid; p < n; p += NT)
+    int16_t *gh = a.fields ? a.fields + (size_t)r * np : nullptr;   // null: the layout keeps no fields
+    for (int p = tid; gh && p < n; p += NT)
         if ((aff[p >> 5] >> (p & 31)) & 1u) {
             int h = 0;
             const uint32_t e1 = a.g.rp[p + 1];

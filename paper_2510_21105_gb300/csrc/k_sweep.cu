@@ -646,6 +646,37 @@ __device__ __forceinline__ void msc_flush_energy(uint32_t (&ebias)[8], int &cnt,
     cnt = 0;
 }
 
+// Two counters of one item (words 1 = c1a, c1b) advanced round by round
+// together, so that the two dependency chains interleave.
+__device__ __forceinline__ void philox_from_shared2(const PhiloxShared &p, uint32_t c1a, uint32_t c1b, uint32_t k0,
+                                                    uint32_t k1, uint4 &ra, uint4 &rb) {
+    uint32_t lo, hi, lo2, hi2;
+    mul_wide(0xD2511F53u, p.u1 ^ c1a, lo, hi);
+    mul_wide(0xD2511F53u, p.u1 ^ c1b, lo2, hi2);
+    uint4 a = make_uint4(p.s0, p.s1, hi ^ p.b ^ (k1 + 0xBB67AE85u), lo);
+    uint4 b = make_uint4(p.s0, p.s1, hi2 ^ p.b ^ (k1 + 0xBB67AE85u), lo2);
+    k0 += 2u * 0x9E3779B9u;
+    k1 += 2u * 0xBB67AE85u;
+    mul_wide(0xCD9E8D57u, a.z, lo, hi);
+    mul_wide(0xCD9E8D57u, b.z, lo2, hi2);
+    a = make_uint4(hi ^ a.y ^ k0, lo, p.h3 ^ a.w ^ k1, p.l3);
+    b = make_uint4(hi2 ^ b.y ^ k0, lo2, p.h3 ^ b.w ^ k1, p.l3);
+#pragma unroll
+    for (int r = 3; r < 10; ++r) {
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+        uint32_t alo0, ahi0, alo1, ahi1, blo0, bhi0, blo1, bhi1;
+        mul_wide(0xD2511F53u, a.x, alo0, ahi0);
+        mul_wide(0xD2511F53u, b.x, blo0, bhi0);
+        mul_wide(0xCD9E8D57u, a.z, alo1, ahi1);
+        mul_wide(0xCD9E8D57u, b.z, blo1, bhi1);
+        a = make_uint4(ahi1 ^ a.y ^ k0, alo1, ahi0 ^ a.w ^ k1, alo0);
+        b = make_uint4(bhi1 ^ b.y ^ k0, blo1, bhi0 ^ b.w ^ k1, blo0);
+    }
+    ra = a;
+    rb = b;
+}
+
 // One (position, word) item of a multi-spin-coded sweep: counts the frustrated
 // bonds of the 32 replicas, decides the 32 attempts and records the energy
 // change of every accepted flip, either in the lane's packed counters ebias
@@ -725,10 +756,13 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
     }
     uint32_t acc32 = 0;
     const uint32_t mq0 = (32u - deg) * 0x01010101u;   // 2c + 32 - deg = m + 32 per byte (PK)
+    uint4 upair[2];
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
         const uint32_t mb = r[g] * (PK ? 8u : 2u) + base * 0x01010101u;
-        const uint4 u = philox_from_shared(ps, (uint32_t)(blk * 8 + g), a.key0, a.key1);
+        if ((g & 1) == 0)
+            philox_from_shared2(ps, (uint32_t)(blk * 8 + g), (uint32_t)(blk * 8 + g + 1), a.key0, a.key1, upair[0], upair[1]);
+        const uint4 u = upair[g & 1];
         const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
         uint32_t ag = 0;   // acceptances of the group, one bit per byte
         if (PK) {

@@ -865,7 +865,8 @@ int enqueue_step(pa_ctx *c, int32_t k, cudaStream_t st, bool time_sweep) {
         na.g = g;
         na.pos = c->d_pos.as<int32_t>();
         na.spins = r.spins[nxt].as<int8_t>();
-        na.fields = r.fields[nxt].as<int16_t>();
+        const bool msc_run = r.variant == PA_VARIANT_MSC || r.variant == PA_VARIANT_MSC_PAIR;
+        na.fields = msc_run ? nullptr : r.fields[nxt].as<int16_t>();   // multi-spin-coded sweeps read no fields
         na.E = r.E[nxt].as<int32_t>();
         na.R = r.R;
         na.k = k;

@@ -17,7 +17,7 @@ struct NlmArgs {
     GraphDev g;
     const int32_t *pos;            // [n] position of each vertex
     int8_t *spins;                 // population after the sweeps of step k
-    int16_t *fields;
+    int16_t *fields;               // rebuilt after a move; null when the sweep layout keeps no fields
     int32_t *E;
     int32_t R, k;
     uint32_t key0, key1;
