@@ -168,27 +168,56 @@ __device__ __forceinline__ int32_t systematic_count(unsigned long long P, int32_
 
 __global__ void k_rs_parents(ResampleArgs a) {
     if (a.active && !a.active[a.k]) return;
-    __shared__ double tree[256];
     __shared__ unsigned long long sh_T, sh_off;
     __shared__ uint32_t sh_o;
-    if (threadIdx.x == 0) {
-        int L = 1;
-        while (L < a.nch) L <<= 1;
-        for (int c = 0; c < L; ++c) tree[c] = c < a.nch ? a.partA[c] : 0.0;
-        for (; L > 1; L >>= 1)
-            for (int i = 0; i < L / 2; ++i) tree[i] = __dadd_rn(tree[2 * i], tree[2 * i + 1]);
+    if (threadIdx.x < 32) {   // warp 0: totals over the chunks
+        const int lane = threadIdx.x;
+        // T and this chunk's offset: integer sums, in any order.
         unsigned long long T = 0, off = 0;
-        for (int c = 0; c < a.nch; ++c) {
-            if (c == (int)blockIdx.x) off = T;
-            T += a.partT[c];
+        for (int c = lane; c < a.nch; c += 32) {
+            const unsigned long long t = a.partT[c];
+            T += t;
+            off += c < (int)blockIdx.x ? t : 0ull;
         }
-        sh_T = T;
-        sh_off = off;
-        sh_o = philox10(make_uint4(0u, 0u, (uint32_t)a.k, TAG_RESAMPLE), a.key0, a.key1).x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            T += __shfl_xor_sync(0xFFFFFFFFu, T, d);
+            off += __shfl_xor_sync(0xFFFFFFFFu, off, d);
+        }
+        // A: the pairwise tree over the chunk sums padded with zeros to a power
+        // of two L <= 256. Lane l holds the aligned block of B = max(L/32, 1)
+        // chunks starting at l B: the tree levels inside the block run in the
+        // lane, the remaining levels pair lanes l and l ^ d, so every level adds
+        // elements 2i and 2i + 1 of the level below, as the sequential tree does.
+        double A = 0.0;
         if (blockIdx.x == 0) {
-            a.recA[a.k] = tree[0];
-            a.recT[a.k] = T;
-            a.reco[a.k] = sh_o;
+            int L = 1;
+            while (L < a.nch) L <<= 1;
+            const int B = L > 32 ? L / 32 : 1;
+            double v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = lane * B + j;
+                v[j] = (j < B && c < a.nch) ? a.partA[c] : 0.0;
+            }
+#pragma unroll
+            for (int w = 1; w < 8; w <<= 1)
+#pragma unroll
+                for (int j = 0; j < 8; j += 2 * w)
+                    if (w < B) v[j] = __dadd_rn(v[j], v[j + w]);
+            A = v[0];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) A = __dadd_rn(A, __shfl_xor_sync(0xFFFFFFFFu, A, d));
+        }
+        if (lane == 0) {
+            sh_T = T;
+            sh_off = off;
+            sh_o = philox10(make_uint4(0u, 0u, (uint32_t)a.k, TAG_RESAMPLE), a.key0, a.key1).x;
+            if (blockIdx.x == 0) {
+                a.recA[a.k] = A;
+                a.recT[a.k] = T;
+                a.reco[a.k] = sh_o;
+            }
         }
     }
     __syncthreads();
