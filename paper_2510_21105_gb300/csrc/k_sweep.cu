@@ -591,30 +591,6 @@ __device__ __forceinline__ PhiloxShared philox_shared(uint32_t c0, uint32_t c2, 
     return p;
 }
 
-__device__ __forceinline__ uint4 philox_from_shared(const PhiloxShared &p, uint32_t c1, uint32_t k0, uint32_t k1) {
-    // round 1 (only word 0 depends on c1)
-    const uint32_t n0 = p.u1 ^ c1;
-    // round 2: word 2 product shared (s0, s1); word 0 product per counter
-    uint32_t lo, hi;
-    mul_wide(0xD2511F53u, n0, lo, hi);
-    uint4 c = make_uint4(p.s0, p.s1, hi ^ p.b ^ (k1 + 0xBB67AE85u), lo);
-    // round 3: word 0 product shared (h3, l3)
-    k0 += 2u * 0x9E3779B9u;
-    k1 += 2u * 0xBB67AE85u;
-    mul_wide(0xCD9E8D57u, c.z, lo, hi);
-    c = make_uint4(hi ^ c.y ^ k0, lo, p.h3 ^ c.w ^ k1, p.l3);
-#pragma unroll
-    for (int r = 3; r < 10; ++r) {
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-        uint32_t lo0, hi0, lo1, hi1;
-        mul_wide(0xD2511F53u, c.x, lo0, hi0);
-        mul_wide(0xCD9E8D57u, c.z, lo1, hi1);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-    }
-    return c;
-}
-
 // Energy bookkeeping of the multi-spin-coded kernels. With |m| <= 31
 // (NPL <= 5) every item adds, per replica 4g + q, 32 + m for an accepted flip
 // and 32 for a rejected attempt into byte q of the lane's word ebias[g]; four
@@ -646,8 +622,11 @@ __device__ __forceinline__ void msc_flush_energy(uint32_t (&ebias)[8], int &cnt,
     cnt = 0;
 }
 
-// Two counters of one item (words 1 = c1a, c1b) advanced round by round
-// together, so that the two dependency chains interleave.
+// Philox4x32-10 of two counters of one item (word 1 = c1a, c1b), finished
+// from the shared round-1-3 products and advanced round by round together,
+// so that the two dependency chains interleave. Round 1: only word 0 depends
+// on c1. Round 2: the word-2 product (s0, s1) is shared, the word-0 product
+// is per counter. Round 3: the word-0 product (h3, l3) is shared.
 __device__ __forceinline__ void philox_from_shared2(const PhiloxShared &p, uint32_t c1a, uint32_t c1b, uint32_t k0,
                                                     uint32_t k1, uint4 &ra, uint4 &rb) {
     uint32_t lo, hi, lo2, hi2;
