@@ -152,10 +152,37 @@ __global__ void k_nlm_pair(NlmArgs a, const int32_t *order) {
             gb[i] = lb[i];
         }
     }
+    if (!a.fields) {
+        // Layouts without fields: only the energies change. Flipping C in
+        // both replicas exchanges their values on C, so E_a + E_b is unchanged,
+        // and replica a changes by the bonds that cross the boundary of C:
+        // with the flipped values x', dE_a = 2 sum_{i in C, j not in C} w_ij x'_i x'_j.
+        long long d = 0;
+        for (int p = tid; p < n; p += NT)
+            if ((vis[p >> 5] >> (p & 31)) & 1u) {
+                const int xi = xa[p];
+                const uint32_t e1 = a.g.rp[p + 1];
+                for (uint32_t e = a.g.rp[p]; e < e1; ++e) {
+                    const int j = a.g.col[e];
+                    if (!((vis[j >> 5] >> (j & 31)) & 1u)) d += (long long)((a.g.wt ? (int)a.g.wt[e] : 1) * xi * xa[j]);
+                }
+            }
+        for (int off = 16; off; off >>= 1) d += __shfl_xor_sync(0xFFFFFFFFu, d, off);
+        if ((tid & 31) == 0) sh_E[0][tid >> 5] = d;
+        __syncthreads();
+        if (tid == 0) {
+            long long t = 0;
+            for (int w = 0; w < NT / 32; ++w) t += sh_E[0][w];
+            a.E[sa] += (int32_t)(2 * t);
+            a.E[sb] -= (int32_t)(2 * t);
+            atomicAdd(&a.pairs[a.k], 1);
+            atomicAdd(&a.flips[a.k], (unsigned long long)csize);
+        }
+        return;
+    }
     // Fields and energies of both replicas, recomputed.
     long long Ea = 0, Eb = 0;
-    int16_t *fa = a.fields ? a.fields + (size_t)sa * np : nullptr;
-    int16_t *fb = a.fields ? a.fields + (size_t)sb * np : nullptr;
+    int16_t *fa = a.fields + (size_t)sa * np, *fb = a.fields + (size_t)sb * np;
     for (int p = tid; p < np; p += NT) {
         int ha = 0, hb = 0;
         if (p < n) {
@@ -169,10 +196,8 @@ __global__ void k_nlm_pair(NlmArgs a, const int32_t *order) {
             Ea += (long long)xa[p] * ha;
             Eb += (long long)xb[p] * hb;
         }
-        if (a.fields) {   // layouts that keep fields (the multi-spin-coded ones do not)
-            fa[p] = (int16_t)ha;
-            fb[p] = (int16_t)hb;
-        }
+        fa[p] = (int16_t)ha;
+        fb[p] = (int16_t)hb;
     }
     for (int off = 16; off; off >>= 1) {
         Ea += __shfl_xor_sync(0xFFFFFFFFu, Ea, off);

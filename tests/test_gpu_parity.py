@@ -97,6 +97,19 @@ def test_parity_nonlocal_moves(variant):
     assert_parity(gpu, orc, g, 64, 3)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 3])
+def test_parity_nonlocal_moves_signed(variant):
+    """Houdayer moves on a +-1 torus: the multi-spin-coded layouts update the
+    two energies from the bonds across the cluster boundary, the others
+    recompute fields and energies; both must give the oracle's energies."""
+    g = wl.torus(16, seed=21)
+    betas = wl.linear_betas(0.2, 2.5, 10)
+    gpu = run_gpu(g, betas, 96, 2, seed=4, nlm_period=2, variant=variant)
+    orc = run_oracle(g, betas, 96, 2, seed=4, nlm_period=2)
+    assert orc.step_nlm_pairs.sum() > 0 and orc.step_nlm_flips.sum() > 0
+    assert_parity(gpu, orc, g, 96, 2)
+
+
 @pytest.mark.parametrize("block", [1, 13, 300])
 @pytest.mark.parametrize("variant,field_bits", [(0, 16), (0, 7), (1, 0), (3, 0)],
                          ids=["int16", "packed", "msc", "msc-pair"])
