@@ -55,7 +55,12 @@ typedef struct pa_ctx pa_ctx;
 /* Sweep kernel variants. */
 #define PA_VARIANT_I8 0   /* int8 spins + int16/int8 local fields in shared memory */
 #define PA_VARIANT_MSC 1  /* multi-spin coded: 32 replicas per 32-bit word */
-#define PA_VARIANT_AUTO 2 /* chosen per graph by the built-in tuning table */
+#define PA_VARIANT_AUTO 2 /* chosen per graph and population: multi-spin coded
+                             when the 32-replica words give every SM a word,
+                             the CTA-pair kernel when they cover at least 40%
+                             of the SMs, else the first of the packed byte
+                             layout, int16 fields and multi-spin coding that
+                             fits the graph in shared memory */
 #define PA_VARIANT_MSC_PAIR 3 /* multi-spin coded, one thread-block cluster of two
                                  CTAs per 32-replica word (distributed shared
                                  memory); same results as PA_VARIANT_MSC */
