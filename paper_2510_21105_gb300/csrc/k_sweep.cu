@@ -566,6 +566,49 @@ __device__ __forceinline__ int msc_bit(int r) {   // bit of replica r = 4g + q i
     return 8 * (r & 3) + (r >> 2);
 }
 
+// Rows <-> bit words for 4 positions 4c .. 4c+3. A spin byte is 0x01 (+1) or
+// 0xFF (-1), 0 on padding. Load: per group g the four rows 4g + q give a word
+// y whose byte j holds, in bit q, replica 4g + q at position 4c + j; the
+// multiply by 0x00204081 spreads that nibble so that bit q lands on bit 8q
+// (the four shifted copies do not overlap, so nothing carries), and the shift
+// by g puts it on bit 8q + g of the position's word. Store: the inverse, with
+// byte j of the row word = 0x01 or 0xFF from the spread bit d (0xFF ^ 0xFE d)
+// and 0 on padding positions.
+__device__ __forceinline__ void msc_pack_rows(const int8_t *spins_in, const int32_t *PS, int np, int c,
+                                              uint32_t (&w4)[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w4[j] = 0u;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        uint32_t y = 0u;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t v = __ldg(reinterpret_cast<const uint32_t *>(spins_in + (size_t)PS[4 * g + q] * np + 4 * c));
+            y |= (v & ~(v >> 1) & 0x01010101u) << q;   // bit 0 of each byte set and bit 1 clear: +1
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) w4[j] |= ((((y >> (8 * j)) & 0xFu) * 0x00204081u) & 0x01010101u) << g;
+    }
+}
+
+__device__ __forceinline__ void msc_unpack_rows(const uint32_t (&w4)[4], int8_t *spins_out, int slot0, int np, int n,
+                                                int c) {
+    uint32_t real = 0u;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) real |= (4 * c + j < n ? 0xFFu : 0u) << (8 * j);
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+        uint32_t e = 0u;   // byte q, bit j: replica 4g + q at position 4c + j
+#pragma unroll
+        for (int j = 0; j < 4; ++j) e |= ((w4[j] >> g) & 0x01010101u) << j;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t d = (((e >> (8 * q)) & 0xFu) * 0x00204081u) & 0x01010101u;
+            *reinterpret_cast<uint32_t *>(spins_out + (size_t)(slot0 + 4 * g + q) * np + 4 * c) = ~(d * 0xFEu) & real;
+        }
+    }
+}
+
 // Philox4x32-10 for the eight counters (c0, c1_g, c2, c3) of one item, which
 // differ only in word 1: the products of rounds 1-3 whose inputs do not depend
 // on c1 are computed once (the result is identical to philox10 of each counter).
@@ -815,12 +858,8 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
         if (tid < 32) Eacc[tid] = a.E_in[PS[tid]];
         // Load: 32 int8 spin rows -> one bit word per position.
         for (int c = tid; c < (np >> 2); c += NT) {
-            uint32_t w4[4] = {0u, 0u, 0u, 0u};
-            for (int r = 0; r < 32; ++r) {
-                const uint32_t v = __ldg(reinterpret_cast<const uint32_t *>(a.spins_in + (size_t)PS[r] * np + 4 * c));
-#pragma unroll
-                for (int j = 0; j < 4; ++j) w4[j] |= ((((v >> (8 * j)) & 0xFFu) == 1u) ? 1u : 0u) << msc_bit(r);
-            }
+            uint32_t w4[4];
+            msc_pack_rows(a.spins_in, PS, np, c, w4);
 #pragma unroll
             for (int j = 0; j < 4; ++j) Wsm[4 * c + j] = w4[j];
         }
@@ -885,15 +924,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
             uint32_t w4[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) w4[j] = Wsm[4 * c + j];
-            for (int r = 0; r < 32; ++r) {
-                uint32_t v = 0;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool real = 4 * c + j < n;
-                    v |= (real ? (((w4[j] >> msc_bit(r)) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
-                }
-                *reinterpret_cast<uint32_t *>(a.spins_out + (size_t)(slot0 + r) * np + 4 * c) = v;
-            }
+            msc_unpack_rows(w4, a.spins_out, slot0, np, n, c);
         }
         if (tid < 32) a.E_out[slot0 + tid] = Eacc[tid];
         if (tid == 0 && misc[5]) a.best_rec[blk] = make_int4(misc[0], misc[1], misc[2], misc[3]);
@@ -958,12 +989,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
         __syncthreads();
         if (tid < 32 && rank == 0) Eacc[tid] = a.E_in[PS[tid]];
         for (int c = tid; c < (np >> 2); c += NT) {
-            uint32_t w4[4] = {0u, 0u, 0u, 0u};
-            for (int r = 0; r < 32; ++r) {
-                const uint32_t v = __ldg(reinterpret_cast<const uint32_t *>(a.spins_in + (size_t)PS[r] * np + 4 * c));
-#pragma unroll
-                for (int j = 0; j < 4; ++j) w4[j] |= ((((v >> (8 * j)) & 0xFFu) == 1u) ? 1u : 0u) << msc_bit(r);
-            }
+            uint32_t w4[4];
+            msc_pack_rows(a.spins_in, PS, np, c, w4);
 #pragma unroll
             for (int j = 0; j < 4; ++j) Wsm[4 * c + j] = w4[j];
         }
@@ -1029,15 +1056,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
             uint32_t w4[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) w4[j] = Wsm[4 * c + j];
-            for (int r = 0; r < 32; ++r) {
-                uint32_t v = 0;
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool real = 4 * c + j < n;
-                    v |= (real ? (((w4[j] >> msc_bit(r)) & 1u) ? 0x01u : 0xFFu) : 0u) << (8 * j);
-                }
-                *reinterpret_cast<uint32_t *>(a.spins_out + (size_t)(slot0 + r) * np + 4 * c) = v;
-            }
+            msc_unpack_rows(w4, a.spins_out, slot0, np, n, c);
         }
         if (rank == 0) {
             if (tid < 32) a.E_out[slot0 + tid] = Eacc[tid];

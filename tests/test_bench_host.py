@@ -29,7 +29,9 @@ def test_sweep_roofline_fractions():
     assert r["attempts_per_s_in_kernel"] == pytest.approx(attempts / t)
     smem = attempts * r["smem_bytes_per_attempt"] / t
     assert r["smem_frac"] == pytest.approx(smem / (bench.SMS * 128 * 2000e6))
-    assert r["traffic"] == bench.SWEEP_TRAFFIC[("k_sweep_msc+pair", 256)]
+    assert r["traffic"] == bench.SWEEP_TRAFFIC.get(("k_sweep_msc+pair", 256))
+    packed = bench.sweep_roofline(stats, attempts, {}, ("k_sweep_packed", 128), 12.0, 0.06)
+    assert packed["traffic"] == bench.SWEEP_TRAFFIC[("k_sweep_packed", 128)]
     # a kernel with no ncu capture reports no traffic; no launches, no line
     assert bench.sweep_roofline(stats, attempts, {}, ("k_sweep", 512), 12.0, 0.06)["traffic"] is None
     assert bench.sweep_roofline({"sweep_ms": 0.0, "sweep_launches": 0}, attempts, {}, ("k_sweep", 512), 12.0, 0.06) is None
