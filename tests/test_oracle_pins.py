@@ -5,7 +5,6 @@ brute force or a value the paper prints, so that a dropped term, a wrong sign
 or index, or a transposed operand in the oracle fails here.
 """
 import ctypes as C
-import itertools
 import math
 import os
 import subprocess
