@@ -46,7 +46,10 @@ extern "C" {
 #define PA_EINVAL (-1)   /* invalid argument (graph, schedule, sizes, options) */
 #define PA_ENOMEM (-2)   /* device or host allocation failed */
 #define PA_ECUDA (-3)    /* a CUDA runtime call or kernel launch failed */
-#define PA_ETIMEOUT (-4) /* a bounded device-side wait expired */
+#define PA_ETIMEOUT (-4) /* a served request did not finish within its
+                            timeout (pa_request.timeout_ms). No kernel waits
+                            on a flag, a peer or another kernel, so no
+                            device-side wait returns it */
 #define PA_EBUSY (-5)    /* the server is at its admission limit */
 #define PA_ESTATE (-6)   /* call out of order (e.g. pa_best before any sweep) */
 
@@ -303,6 +306,9 @@ typedef struct {
     int32_t K, R, sweeps;
     uint64_t seed;
     pa_anneal_opts opts;      /* opts.stream is ignored */
+    double timeout_ms;        /* > 0: cancel the request with PA_ETIMEOUT if it
+                                 has not completed this long after admission
+                                 (its enqueued work drains first); 0 = none */
 } pa_request;
 
 typedef struct {
@@ -331,6 +337,15 @@ int pa_server_poll(pa_server *s, uint64_t id, int32_t *state);
 /* Result of a finished request (config: host int8[n] or NULL). PA_EBUSY if
  * it has not finished. */
 int pa_server_result(pa_server *s, uint64_t id, pa_response *out, int8_t *config);
+/* Forget a finished request (its response and configuration); the server
+ * already released its device memory and input copies when it finished.
+ * PA_EBUSY if it has not finished, PA_EINVAL for an unknown id. */
+int pa_server_release(pa_server *s, uint64_t id);
+/* Testing hook for failure handling: while hold != 0 the tick thread enqueues
+ * no further steps of request id, as if the host side of its job had stalled
+ * (work already enqueued completes normally). A held request with a timeout
+ * is cancelled with PA_ETIMEOUT; the others are not affected. */
+int pa_server_hold(pa_server *s, uint64_t id, int32_t hold);
 int pa_server_stats(pa_server *s, pa_server_stats_t *out);
 /* Finish all submitted requests, then stop the thread and free everything. */
 int pa_server_stop(pa_server *s);
@@ -358,12 +373,14 @@ void pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_fn, void *user);
 /* ---------------------------------------------------------------------------
  * Resampling step without any device allocation.
  *
- * The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory: code being recorded into a CUDA graph
- * by stream capture, processes whose device-memory budget is owned by a host
- * framework, and latency-critical loops that forbid allocator calls. It
- * performs the same reweighting and systematic resampling as one temperature
- * step of pa_anneal (weights exp(-(beta_k - beta_prev)(E_r - E_min)) as FP64
+ * The paper has no counterpart to this entry point. It serves callers that
+ * cannot call cudaMalloc: a host framework that owns the whole device-memory
+ * budget through its own pool (a caching allocator that must see every byte,
+ * so a library allocating on the side can push it out of memory), and
+ * latency-critical loops where an allocator call may block, synchronise the
+ * device or fail at a moment the caller cannot handle. It performs the same
+ * reweighting and systematic resampling as one temperature step of
+ * pa_anneal (weights exp(-(beta_k - beta_prev)(E_r - E_min)) as FP64
  * products of squarings, pairwise-tree weight sum, integer weights
  * floor(2^32 w_r), offset word from Philox(0, 0, k, tag 1) keyed by seed) and
  * returns bit-identical copy counts and parents.
@@ -375,7 +392,8 @@ void pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_fn, void *user);
  *   parent    device int32[R]: new slot s receives old slot parent[s]
  *   counts    device int32[R] copy counts, or NULL
  *   out       host result (weight sum A, integer total T, E_min, offset o),
- *             or NULL; when given, the call waits for the stream
+ *             or NULL; when given, the call copies it back and waits for the
+ *             stream; with NULL the call only enqueues work and returns
  *   stream    cudaStream_t, NULL = legacy default stream
  *
  * Scratch lives in a fixed file-scope device array of about 0.6 MB that every
@@ -384,8 +402,9 @@ void pa_set_allocator(pa_alloc_fn alloc, pa_free_fn free_fn, void *user);
  * device looks up that array's device address (cudaGetSymbolAddress) with
  * the device current, so make the first call on each device before any stream
  * capture. All calls share the array and it keeps the last call's contents;
- * calls that overlap on the GPU (other streams, other threads) race on it.
- * Returns PA_OK, PA_EINVAL or PA_ECUDA.
+ * every call writes each scratch word before reading it, so nothing needs
+ * clearing between calls. Calls that overlap on the GPU (other streams, other
+ * threads) race on it. Returns PA_OK, PA_EINVAL or PA_ECUDA.
  */
 #define PA_NOALLOC_MAX_R 32768
 

@@ -65,7 +65,7 @@ class pa_batch_opts(C.Structure):
 class pa_request(C.Structure):
     _fields_ = [("n", C.c_int32), ("row_ptr", C.c_void_p), ("col", C.c_void_p), ("w", C.c_void_p),
                 ("betas", C.c_void_p), ("K", C.c_int32), ("R", C.c_int32), ("sweeps", C.c_int32),
-                ("seed", C.c_uint64), ("opts", pa_anneal_opts)]
+                ("seed", C.c_uint64), ("opts", pa_anneal_opts), ("timeout_ms", C.c_double)]
 
 
 class pa_response(C.Structure):
@@ -133,6 +133,8 @@ def lib():
                 "pa_server_poll": ([vp, u64, C.POINTER(i32)], C.c_int),
                 "pa_server_result": ([vp, u64, C.POINTER(pa_response), vp], C.c_int),
                 "pa_server_stats": ([vp, C.POINTER(pa_server_stats_t)], C.c_int),
+                "pa_server_release": ([vp, u64], C.c_int),
+                "pa_server_hold": ([vp, u64, i32], C.c_int),
                 "pa_server_stop": ([vp], C.c_int),
             }
             for name, (args, res) in sig.items():
@@ -150,7 +152,8 @@ def exported_symbols():
             "pa_best_record", "pa_get_state", "pa_set_state", "pa_energies", "pa_save", "pa_load", "pa_stats",
             "pa_step_stats", "pa_tables", "pa_colouring", "pa_set_allocator", "pa_run_info",
             "pa_resample_noalloc", "pa_batch_anneal", "pa_server_start", "pa_server_submit",
-            "pa_server_poll", "pa_server_result", "pa_server_stats", "pa_server_stop"]
+            "pa_server_poll", "pa_server_result", "pa_server_stats", "pa_server_stop",
+            "pa_server_release", "pa_server_hold"]
 
 
 def strerror(code: int) -> str:
@@ -314,15 +317,17 @@ def pa_colouring(ctx, n: int):
 
 
 def pa_resample_noalloc(energies_ptr: int, R: int, beta_prev: float, beta_k: float, seed: int, k: int,
-                        parent_ptr: int, counts_ptr: int | None = None, stream=None):
+                        parent_ptr: int, counts_ptr: int | None = None, stream=None, want_result: bool = True):
     """Resampling step with caller-owned device buffers and no device allocation
-    (see include/pa.h); pointers are raw device addresses."""
-    res = pa_resample_result()
+    (see include/pa.h); pointers are raw device addresses. With
+    want_result=False the host result is not requested (NULL is passed), so
+    the call only enqueues its kernel and returns None."""
+    res = pa_resample_result() if want_result else None
     _check(lib().pa_resample_noalloc(C.c_void_p(energies_ptr), int(R), float(beta_prev), float(beta_k),
                                      int(seed) & (2**64 - 1), int(k), C.c_void_p(parent_ptr),
-                                     C.c_void_p(counts_ptr) if counts_ptr else None, C.byref(res),
-                                     stream), "pa_resample_noalloc")
-    return dict(A=res.A, T=res.T, emin=res.emin, o=res.o)
+                                     C.c_void_p(counts_ptr) if counts_ptr else None,
+                                     C.byref(res) if want_result else None, stream), "pa_resample_noalloc")
+    return dict(A=res.A, T=res.T, emin=res.emin, o=res.o) if want_result else None
 
 
 def pa_batch_anneal(items, n_streams: int = 0, use_graph: bool = False, stream=None) -> float:
@@ -362,7 +367,8 @@ class Server:
                "pa_server_start")
         self.n = {}
 
-    def submit(self, g, betas, R: int, S: int, seed: int, K: int | None = None, **opts) -> int:
+    def submit(self, g, betas, R: int, S: int, seed: int, K: int | None = None, timeout_ms: float = 0.0,
+               **opts) -> int:
         rp = g.rp_u32
         col = g.col_u16
         w = None if g.w is None else np.ascontiguousarray(g.w, np.int8)
@@ -371,7 +377,8 @@ class Server:
             K = len(b) if b is not None else 0
         req = pa_request(int(g.n), rp.ctypes.data, col.ctypes.data if len(col) else None,
                          None if w is None else w.ctypes.data, None if b is None else b.ctypes.data,
-                         int(K), int(R), int(S), int(seed) & (2**64 - 1), pa_default_opts(**opts))
+                         int(K), int(R), int(S), int(seed) & (2**64 - 1), pa_default_opts(**opts),
+                         float(timeout_ms))
         rid = C.c_uint64()
         _check(lib().pa_server_submit(self.h, C.byref(req), C.byref(rid)), "pa_server_submit")
         self.n[rid.value] = g.n
@@ -392,6 +399,19 @@ class Server:
         out = {name: getattr(r, name) for name, _ in pa_response._fields_}
         out["config"] = cfg
         return out
+
+    def release(self, rid: int) -> bool:
+        """Forget a finished request; False if it has not finished yet."""
+        rc = lib().pa_server_release(self.h, int(rid))
+        if rc == PA_EBUSY:
+            return False
+        _check(rc, "pa_server_release")
+        self.n.pop(rid, None)
+        return True
+
+    def hold(self, rid: int, hold: bool = True):
+        """Testing hook: stop (or resume) enqueuing the request's steps."""
+        _check(lib().pa_server_hold(self.h, int(rid), int(bool(hold))), "pa_server_hold")
 
     def stats(self) -> dict:
         st = pa_server_stats_t()

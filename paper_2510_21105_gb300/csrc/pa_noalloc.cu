@@ -1,10 +1,10 @@
 // pa_noalloc.cu -- pa_resample_noalloc(): one resampling step that allocates
-// no memory. For callers that cannot call cudaMalloc: code recorded into a
-// CUDA graph by stream capture, processes whose device-memory budget is owned
-// by a host framework, and latency-critical loops that forbid allocator
-// calls. The caller passes the energies and receives the parents and copy
-// counts in its own device buffers; every intermediate array lives in one
-// file-scope __device__ scratch buffer of fixed size, shared by all calls.
+// no memory. For callers that cannot call cudaMalloc: a host framework that
+// owns the device-memory budget through its own pool, and latency-critical
+// loops where an allocator call may block, synchronise or fail. The caller
+// passes the energies and receives the parents and copy counts in its own
+// device buffers; every intermediate array lives in one file-scope __device__
+// scratch buffer of fixed size, shared by all calls.
 #include <cuda_runtime.h>
 
 #include <cmath>
