@@ -172,10 +172,10 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ ours ---
-# DRAM bytes (read + write) of one sweep launch on this workload, from the ncu
-# captures summarised in profiles/ (sweep_packed_g63like.md); reported only
-# while the captured kernel is the one that runs. The multi-spin-coded kernels
-# changed after their last capture, so they report none.
+# DRAM bytes (read + write) of one sweep launch on this workload, from one ncu
+# capture of the kernel; reported only while the captured kernel is the one
+# that runs. The multi-spin-coded kernels changed after their last capture, so
+# they report none.
 SWEEP_TRAFFIC = {("k_sweep_packed", 128): 334.719744e6 + 289.454080e6}
 OPS_PER_ATTEMPT = 20.0   # a quarter Philox4x32-10 block (15) + decision (4) + flip updates (~1)
 INT_LANES_PER_SM = 128   # ALU pipe (LOP3/IADD3) 64 + FMA pipe (IMAD) 64

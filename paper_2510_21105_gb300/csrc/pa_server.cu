@@ -10,7 +10,12 @@
 //               enqueued; a request keeps at most two ticks in flight, so
 //               arrivals join within one tick;
 //   completion  a request whose last tick has finished on the device records
-//               its best cut and configuration and releases its memory.
+//               its best cut and configuration and releases its memory and
+//               its copies of the caller's inputs;
+//   timeout     a request with timeout_ms > 0 that has not completed that
+//               long after its admission is cancelled: its enqueued ticks
+//               drain (every kernel is bounded), its memory is released and
+//               it reports PA_ETIMEOUT; the other requests carry on.
 // Populations stay resident between ticks. Results are bit-identical to a
 // lone pa_anneal of the same request: all randomness is keyed by seed, slot,
 // step, sweep and vertex, never by scheduling.
@@ -45,8 +50,10 @@ struct Request {
     int32_t K = 0, R = 0, S = 0;
     uint64_t seed = 0;
     pa_anneal_opts opts{};
+    double timeout_ms = 0.0;
     size_t bytes = 0;
     // state
+    bool held = false;               // testing hook: no further ticks are enqueued
     pa_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;   // one stream per admitted request
     int32_t k_enq = 0;
@@ -127,6 +134,11 @@ void finish(pa_server *s, Request &q, int status) {
         cudaStreamDestroy(q.stream);
         q.stream = nullptr;
     }
+    // The inputs are not needed any more; only the response and configuration stay.
+    std::vector<uint32_t>().swap(q.rp);
+    std::vector<uint16_t>().swap(q.col);
+    std::vector<int8_t>().swap(q.w);
+    std::vector<double>().swap(q.betas);
     q.resp.finish_ms = ms_since(s);
     q.resp.status = status == 2 ? PA_OK : status;
     std::lock_guard<std::mutex> lock(s->mu);
@@ -216,6 +228,9 @@ void worker_loop(pa_server *s) {
             if (q->k_enq >= q->K && q->inflight.empty()) {
                 finish(s, *q, 2);
                 progressed = true;
+            } else if (q->timeout_ms > 0.0 && ms_since(s) - q->resp.start_ms > q->timeout_ms) {
+                finish(s, *q, PA_ETIMEOUT);   // pa_destroy waits for the enqueued ticks
+                progressed = true;
             }
         }
         {
@@ -227,7 +242,12 @@ void worker_loop(pa_server *s) {
         }
         if (progressed) s->cv.notify_all();
         for (auto &q : act) {
-            if (q->k_enq >= q->K || q->inflight.size() >= 2) continue;
+            bool held;
+            {
+                std::lock_guard<std::mutex> lock(s->mu);
+                held = q->held;
+            }
+            if (held || q->k_enq >= q->K || q->inflight.size() >= 2) continue;
             const int32_t k_end = std::min(q->K, q->k_enq + s->steps_per_tick);
             if (pa_anneal_run(q->ctx, k_end) != PA_OK) {
                 finish(s, *q, PA_ECUDA);
@@ -266,7 +286,7 @@ int pa_server_start(pa_server **out, size_t hbm_budget_bytes, int32_t n_streams,
 
 int pa_server_submit(pa_server *s, const pa_request *req, uint64_t *id) {
     if (!s || !req || !req->row_ptr || req->n < 1 || req->n > 65536 || req->R < 1 || req->K < 0 ||
-        req->sweeps < 0 || (!req->opts.adaptive && req->K > 0 && !req->betas))
+        req->sweeps < 0 || (!req->opts.adaptive && req->K > 0 && !req->betas) || !(req->timeout_ms >= 0.0))
         return PA_EINVAL;
     auto q = std::make_shared<Request>();
     q->n = req->n;
@@ -284,6 +304,7 @@ int pa_server_submit(pa_server *s, const pa_request *req, uint64_t *id) {
     q->S = req->sweeps;
     q->seed = req->seed;
     q->opts = req->opts;
+    q->timeout_ms = req->timeout_ms;
     q->bytes = estimate_bytes(*q);
     {
         std::lock_guard<std::mutex> lock(s->mu);
@@ -319,6 +340,25 @@ int pa_server_result(pa_server *s, uint64_t id, pa_response *out, int8_t *config
     *out = q.resp;
     if (config && !q.config.empty()) std::memcpy(config, q.config.data(), q.config.size());
     return q.status == 2 ? PA_OK : q.status;
+}
+
+int pa_server_release(pa_server *s, uint64_t id) {
+    if (!s) return PA_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return PA_EINVAL;
+    if (it->second->status == 0 || it->second->status == 1) return PA_EBUSY;
+    s->all.erase(it);
+    return PA_OK;
+}
+
+int pa_server_hold(pa_server *s, uint64_t id, int32_t hold) {
+    if (!s) return PA_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->all.find(id);
+    if (it == s->all.end()) return PA_EINVAL;
+    it->second->held = hold != 0;
+    return PA_OK;
 }
 
 int pa_server_stats(pa_server *s, pa_server_stats_t *out) {

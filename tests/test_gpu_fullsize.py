@@ -83,6 +83,46 @@ def test_replay_torus100_full_population(variant):
     _replay_check(g, betas, c["R"], c["S"], c["seed"], 4, subset, variant=variant)
 
 
+def test_replay_g63like_late_beta_default_layout():
+    """Step 899 (beta = 3.61) of the benchmarked anneal in its own launch
+    configuration: default layout (456 words in one-CTA blocks + 56 in CTA
+    pairs), Houdayer moves every 50 steps before it. Low acceptance: most
+    thresholds of the step's table are 0 ("never")."""
+    c = wl.CONFIGS["g63like"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    k = 899
+    T = oracle.accept_table(betas[k], g.maxdeg)
+    assert (T[4:] == 0).all() and T[1] > 0
+    subset = np.array([0, 1, 2, 3, 31, 4097, 8190, 12345, 14591, 14592, 15000, 16383])
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], k, subset, nlm_period=c["nlm_period"])
+
+
+def test_replay_g63like_late_nonlocal_step():
+    """Step 900 (beta = 3.61), a non-local step late in the benchmarked anneal,
+    default layout: resampling, sweeps and Houdayer moves of sampled pairs."""
+    c = wl.CONFIGS["g63like"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    k = 900
+    assert k % c["nlm_period"] == 0
+    order = oracle.nlm_order(c["R"], c["seed"], k)
+    subset = np.array(sorted(order[[0, 1, 5000, 5001, 9998, 9999, 16382, 16383]].tolist()))
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], k, subset, nlm_period=c["nlm_period"])
+
+
+@pytest.mark.parametrize("variant", [1, 3])
+def test_replay_torus100_late_beta(variant):
+    """Step 700 (beta = 3.08) of the 100 x 100 signed torus at R = 32768 in the
+    multi-spin-coded kernels (one-CTA head + CTA-pair tail, and CTA pairs
+    only)."""
+    c = wl.CONFIGS["torus100"]
+    g = c["graph"]()
+    betas = wl.linear_betas(*c["beta"], c["K"])
+    subset = np.array([0, 5, 31, 32, 9999, 20000, 29183, 29184, 32767])
+    _replay_check(g, betas, c["R"], c["S"], c["seed"], 700, subset, variant=variant)
+
+
 def test_full_g63like_anneal_properties():
     """The whole benchmarked anneal: invariants that hold at any size."""
     c = wl.CONFIGS["g63like"]

@@ -1,11 +1,12 @@
 """Serving loop (pa_server_*): requests admitted by device-memory budget while
-others run produce results bit-identical to the same requests run alone."""
+others run produce results bit-identical to the same requests run alone, and
+each request run alone is bit-identical to the oracle."""
 import time
 
 import numpy as np
 import pytest
 
-from gpu_helpers import require_gpu
+from gpu_helpers import assert_parity, require_gpu, run_gpu, run_oracle
 from paper_2510_21105_gb300 import binding as B
 from paper_2510_21105_gb300 import workloads as wl
 
@@ -21,6 +22,16 @@ def _requests():
         (wl.gnm(1200, 6000, seed=15), wl.linear_betas(0.1, 2.0, 15), 64, 5, 5, dict()),
         (wl.torus(30, seed=16), wl.linear_betas(0.1, 3.0, 35), 200, 2, 6, dict()),
     ]
+
+
+def test_each_request_alone_matches_oracle():
+    """Every request of the served mix, run alone, against the oracle element by
+    element (spins, energies, per-step records, copy counts, best record)."""
+    require_gpu()
+    for g, betas, R, S, seed, kw in _requests():
+        gpu = run_gpu(g, betas, R, S, seed, **kw)
+        orc = run_oracle(g, betas, R, S, seed, **{k: v for k, v in kw.items() if k == "nlm_period"})
+        assert_parity(gpu, orc, g, R, S)
 
 
 def _alone(g, betas, R, S, seed, kw):
