@@ -181,8 +181,11 @@ void pa_destroy(pa_ctx *ctx);
  * the population from beta_{k-1} to beta_k (beta_{-1} = 0, the initial i.i.d.
  * uniform population being exact at beta = 0), runs `sweeps` Metropolis
  * sweeps at beta_k (colour classes in order; a flip with energy change
- * dE = 2m is accepted iff m <= 0 or u < floor(2^32 exp(-2 beta_k m)), u the
- * Philox word of (spin, slot, step, sweep)), records the best energy after
+ * dE = 2m is accepted iff m <= 0 or u < floor(2^32 exp(-2 beta_k m)), u a
+ * uniform 32-bit integer whose top byte is byte slot%4 of word (slot/4)%4 of
+ * Philox(vertex, slot/16, step, sweep) and whose low 24 bits, read only when
+ * the top byte ties with the threshold's, are the top 24 bits of word slot%4
+ * of Philox(vertex, slot/4, step, tag 4 | sweep)), records the best energy after
  * every sweep, and applies the non-local move when due.
  * betas: host array of K finite, non-negative, non-decreasing doubles
  * (ignored, may be NULL, when opts->adaptive = 1; K is then the maximum

@@ -82,6 +82,7 @@ def lib():
             L.orc_block_move.argtypes = [i32, vp, vp, vp, vp, vp, i32, dbl, i32, C.c_uint32, vp]
             L.orc_block_move.restype = i32
             L.orc_step.restype = C.c_int
+            L.orc_sweep_uniforms.argtypes = [u64, i32, vp, vp, i32, i32, vp]
         return _lib
 
 
@@ -102,6 +103,16 @@ def philox4x32_10(ctr, key):
     out = np.zeros(4, np.uint32)
     lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
     return out
+
+
+def sweep_uniforms(seed: int, vertices, slots, k: int, s: int):
+    """The 32-bit uniforms of Metropolis attempts (vertex, replica) at step k,
+    sweep s (``orc_sweep_uniforms``)."""
+    i = np.ascontiguousarray(vertices, dtype=np.int32)
+    r = np.ascontiguousarray(slots, dtype=np.int32)
+    u = np.zeros(len(i), np.uint32)
+    lib().orc_sweep_uniforms(int(seed), len(i), _p(i), _p(r), int(k), int(s), _p(u))
+    return u
 
 
 def energy(rp, col, w, x) -> int:

@@ -89,7 +89,7 @@ void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t ou
 }
 
 /* Stream tags (top four bits of counter word 3). */
-enum { TAG_SWEEP = 0, TAG_RESAMPLE = 1, TAG_NONLOCAL = 2, TAG_INIT = 3 };
+enum { TAG_SWEEP = 0, TAG_RESAMPLE = 1, TAG_NONLOCAL = 2, TAG_INIT = 3, TAG_TAIL = 4 };
 
 /* One 32-bit random word: word `w` of Philox(key = seed, counter = c). */
 static uint32_t rng_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
@@ -493,6 +493,31 @@ static void free_view(graph_view *g)
     free(g->class_list);
 }
 
+/* The 32-bit uniform of a Metropolis attempt on vertex i of replica `slot`
+ * at step k, sweep s. Its top 8 bits are byte (slot mod 4) of word
+ * (floor(slot/4) mod 4) of Philox(i, floor(slot/16), k, s), so one Philox
+ * call serves 16 replicas; its low 24 bits are the top 24 bits of word
+ * (slot mod 4) of Philox(i, floor(slot/4), k, tag 4 | s). Both are uniform
+ * and independent, so u is uniform on [0, 2^32). A comparison u < T needs
+ * the low 24 bits only when the top byte of u equals that of T. */
+static uint32_t sweep_uniform(uint64_t seed, int32_t i, int32_t slot, int32_t k, int32_t s)
+{
+    uint32_t word = rng_word(seed, (uint32_t)i, (uint32_t)slot >> 4, (uint32_t)k,
+                             ((uint32_t)TAG_SWEEP << 28) | (uint32_t)s, (slot >> 2) & 3);
+    uint32_t top = (word >> (8 * (slot & 3))) & 0xFFu;
+    uint32_t tail = rng_word(seed, (uint32_t)i, (uint32_t)slot >> 2, (uint32_t)k,
+                             ((uint32_t)TAG_TAIL << 28) | (uint32_t)s, slot & 3);
+    return (top << 24) | (tail >> 8);
+}
+
+/* Uniforms of n attempts (vertex i[t], replica slot[t]) at step k, sweep s,
+ * for the tests. */
+void orc_sweep_uniforms(uint64_t seed, int32_t n, const int32_t *i, const int32_t *slot, int32_t k,
+                        int32_t s, uint32_t *u)
+{
+    for (int32_t t = 0; t < n; ++t) u[t] = sweep_uniform(seed, i[t], slot[t], k, s);
+}
+
 /* One Metropolis sweep of replica `slot` at step k, sweep index s: colours in
  * order, vertices ascending within a colour. The field h_i is recomputed
  * from the neighbours at every visit. Returns the number of accepted flips
@@ -507,11 +532,7 @@ static int64_t sweep_replica(const graph_view *g, int8_t *x, int32_t *E, const u
             int32_t h = local_field(g->rp, g->col, g->w, x, i);
             int32_t m = -x[i] * h;            /* dE = 2m for flipping x_i */
             int accept = m <= 0;
-            if (!accept) {
-                uint32_t u = rng_word(seed, (uint32_t)i, (uint32_t)slot >> 2, (uint32_t)k,
-                                      ((uint32_t)TAG_SWEEP << 28) | (uint32_t)s, slot & 3);
-                accept = u < T[m];
-            }
+            if (!accept) accept = sweep_uniform(seed, i, slot, k, s) < T[m];
             if (accept) {
                 x[i] = (int8_t)-x[i];
                 *E += 2 * m;

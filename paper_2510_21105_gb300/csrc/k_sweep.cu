@@ -12,9 +12,10 @@
 // parallel (one thread per (position, group)); the accepted flips push
 // +-2 into the neighbours' fields with one packed 32-bit shared atomic per
 // neighbour and group (the bias keeps every lane non-negative, so the packed
-// add never carries across lanes). One Philox4x32-10 call yields the four
-// uniforms of the group: word q of Philox(counter = (vertex, slot/4, step,
-// sweep)) belongs to slot 4*(slot/4) + q.
+// add never carries across lanes). The top bytes of the group's four
+// uniforms are the bytes of one word of Philox(counter = (vertex, slot/16,
+// step, sweep)): byte q of word (slot/4) % 4 belongs to slot 4*(slot/4) + q;
+// the low 24 bits are drawn only when a top byte ties with the threshold's.
 // The block is loaded from the parents chosen by the resampling (the copy of
 // the resampling is fused into this load) and written to the next buffers.
 #include <cooperative_groups.h>
@@ -65,12 +66,14 @@ __device__ __forceinline__ void sweep_item(uint32_t *__restrict__ Ssm, uint32_t 
             h = (int)((hw0 >> (8 * q)) & 0xFFu) - 128;
         m[q] = x[q] > 0 ? -h : h;   // dE = -2 x h = 2m
     }
-    const uint4 u = philox10(make_uint4(__ldg(&a.g.vid[p]), c1, (uint32_t)a.k, c3), a.key0, a.key1);
-    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+    // Top bytes of the four uniforms: word c1 & 3 of the call of slots 16 (c1 >> 2) ..
+    const uint32_t vid = __ldg(&a.g.vid[p]);
+    const uint32_t uw = word_of(philox10(make_uint4(vid, c1 >> 2, (uint32_t)a.k, c3), a.key0, a.key1), c1 & 3u);
     uint32_t acc = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const bool ok = (m[q] <= 0) || (uu[q] < Tt[min(m[q], a.g.mmax)]);
+        const bool ok = (m[q] <= 0) || accept_by_top_byte((uw >> (8 * q)) & 0xFFu, Tt[min(m[q], a.g.mmax)], vid,
+                                                          4u * c1 + q, (uint32_t)a.k, c3, a.key0, a.key1);
         acc |= (uint32_t)ok << q;
     }
     if (acc) {
@@ -306,13 +309,13 @@ __device__ __forceinline__ void pk_decide(const uint32_t *__restrict__ Bsm, cons
     const uint32_t smask = b & 0x01010101u;
     const uint32_t hb = (b & 0xFEFEFEFEu) | (par * 0x01010101u);
     const uint32_t mb = (hb ^ (smask * 0xFFu)) + smask;
-    const uint4 u = philox10(make_uint4(vid, c1, (uint32_t)a.k, c3), a.key0, a.key1);
-    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
+    const uint32_t uw = word_of(philox10(make_uint4(vid, c1 >> 2, (uint32_t)a.k, c3), a.key0, a.key1), c1 & 3u);
     uint32_t acc = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
-        const bool ok = (idx <= 128u) | (uu[q] < T256[idx]);
+        const bool ok = (idx <= 128u) || accept_by_top_byte((uw >> (8 * q)) & 0xFFu, T256[idx], vid, 4u * c1 + q,
+                                                            (uint32_t)a.k, c3, a.key0, a.key1);
         acc |= (uint32_t)ok << q;
     }
     it.b = b;
@@ -553,15 +556,32 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
 // +1 to m_r = -x_p h_p; a bit-sliced counter over the neighbours (carry-save
 // adders, four bonds per step) gives c_r and m_r = 2 c_r - deg(p). An 8 x 8
 // bit transpose in every byte lane turns the counter planes into one byte per
-// replica, group by group, and each group is decided exactly like the packed
-// layout (same thresholds, same Philox word (vertex, slot/4, step, sweep)).
-// With |m| <= 31 the byte holds 4m + 128, which is also the byte offset of
-// the entry of m in a table kept at the start of shared memory, so the lookup
-// needs no address arithmetic. The entry is 2^64 - T[m] split into a low word
-// (offset 4m + 128) and a high word (256 bytes further), with T = 2^32 for
-// m <= 0 (always accepted) and 0 kept as 0 (never accepted): the high word of
-// u + entry is all ones exactly when u < T[m], so one 64-bit add decides an
-// attempt, the m <= 0 rule included. Accepted replicas flip with one XOR.
+// replica, group by group. The uniforms of the group's four replicas have
+// their top bytes in one Philox word (word g & 3 of the call of slots
+// 16 (slot >> 4) ..): byte q belongs to replica 4g + q, the same byte as its
+// count. With |m| <= 31 the count byte holds 4m + 128, which is also the byte
+// offset of the entry of m in a table kept at the start of shared memory, so
+// the lookup needs no address arithmetic (wider counts: m + 128, a word index).
+// An entry holds a 16-bit value E(m) in both halves. Two replicas are decided
+// by one 32-bit multiply-add in 16-bit lanes, lane = 128 top + E(m):
+//   E = 0x8000 - 128 t8 (t8 = T[m] >> 24):  lane < 0x8000 iff top < t8 (accept),
+//                                           lane = 0x8000 iff top = t8 (tie),
+//   + 64 when T[m] has no low bits (a tie rejects), 0x8040 when T[m] = 0,
+//   1 for m <= 0 (always accepted).
+// Every lane stays in [1, 0xFFC0], so lanes never carry into each other; bit
+// 15 of a lane is "reject or tie" and bit 15 of lane - 1 is "reject". A byte
+// permute replicating those sign bits turns the four lanes of a group into
+// byte masks. A tie (probability 1/256 per uncertain attempt) is settled by
+// the low 24 bits of the uniform, drawn only then. Accepted replicas flip
+// with one XOR.
+// Byte permute with sign replication: each selector nibble with bit 3 set
+// fills its result byte with the top bit of the selected byte.
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
 __device__ __forceinline__ int msc_bit(int r) {   // bit of replica r = 4g + q in a word
     return 8 * (r & 3) + (r >> 2);
 }
@@ -704,6 +724,18 @@ __device__ __forceinline__ void philox_from_shared2(const PhiloxShared &p, uint3
 // change of every accepted flip, either in the lane's packed counters ebias
 // (MscPackedE) or by a shared atomic on Eacc (local or a cluster peer's shared
 // memory). Returns the mask of accepted replicas.
+// Entry i of the decision table: E(m) in both 16-bit halves, m = i - 32 for
+// counts of |m| <= 31 (byte offset 4m + 128), else m = i - 128 (word index).
+__device__ __forceinline__ uint32_t msc_entry(int i, bool pk, const uint32_t *tab, int mmax) {
+    const int m = pk ? i - 32 : i - 128;
+    uint32_t e = 1u;   // m <= 0: always accepted
+    if (m > 0) {
+        const uint32_t T = m <= mmax ? tab[m] : 0u;
+        e = T == 0u ? 0x8040u : 0x8000u - 128u * (T >> 24) + ((T & 0xFFFFFFu) == 0u ? 64u : 0u);
+    }
+    return e * 0x00010001u;
+}
+
 template <int NPL, bool WEIGHTED>
 __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t *Wsm, const uint32_t *T256, int p,
                                              uint32_t x, uint32_t c3, int blk, int32_t *Eacc,
@@ -753,7 +785,10 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
     const uint32_t deg = e1 - e0;
     constexpr bool PK = MscPackedE<NPL>::value;
     const uint32_t base = PK ? 128u - 4u * deg : 128u - deg;   // mb byte = 4m + 128 (PK, deg <= 31) or m + 128
-    const PhiloxShared ps = philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1);
+    // Both Philox calls of the item (slots 32 blk .. +15 and +16 .. +31).
+    uint4 u0, u1;
+    philox_from_shared2(philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1), 2u * blk, 2u * blk + 1u, a.key0,
+                        a.key1, u0, u1);
     // Byte q of r[g] = c of replica 4g + q: an 8 x 8 bit transpose in every byte lane.
     uint32_t r[8];
 #pragma unroll
@@ -776,41 +811,54 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
         r[b] ^= t << 1;
         r[b + 1] ^= t;
     }
-    uint32_t acc32 = 0;
+    uint32_t acc32 = 0, acct32 = 0;   // accepted; accepted or tied
     const uint32_t mq0 = (32u - deg) * 0x01010101u;   // 2c + 32 - deg = m + 32 per byte (PK)
-    uint4 upair[2];
+    const unsigned char *tb = reinterpret_cast<const unsigned char *>(T256);
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
         const uint32_t mb = r[g] * (PK ? 8u : 2u) + base * 0x01010101u;
-        if ((g & 1) == 0)
-            philox_from_shared2(ps, (uint32_t)(blk * 8 + g), (uint32_t)(blk * 8 + g + 1), a.key0, a.key1, upair[0], upair[1]);
-        const uint4 u = upair[g & 1];
-        const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-        uint32_t ag = 0;   // acceptances of the group, one bit per byte
-        if (PK) {
-            uint32_t acc[4];   // all ones iff accepted: high word of u + (2^64 - threshold)
+        const uint4 &uq = g < 4 ? u0 : u1;
+        const uint32_t uw = (g & 3) == 0 ? uq.x : (g & 3) == 1 ? uq.y : (g & 3) == 2 ? uq.z : uq.w;
+        uint32_t e[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const unsigned char *tb = reinterpret_cast<const unsigned char *>(T256) + ((mb >> (8 * q)) & 0xFFu);
-                const uint32_t lo = *reinterpret_cast<const uint32_t *>(tb), hi = *reinterpret_cast<const uint32_t *>(tb + 256);
-                acc[q] = (uint32_t)(((unsigned long long)uu[q] + (((unsigned long long)hi << 32) | lo)) >> 32);
-            }
-            const uint32_t A = __byte_perm(__byte_perm(acc[0], acc[1], 0x0040u), __byte_perm(acc[2], acc[3], 0x0040u), 0x5410u);
-            acc32 |= A & (0x01010101u << g);
-            ebias[g] += ((r[g] * 2u + mq0) & A) | (0x20202020u & ~A);   // byte q: accepted ? 32 + m : 32
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
-                ag |= (uint32_t)((idx <= 128u) | (uu[q] < T256[idx])) << (8 * q);
-            }
-            acc32 |= ag << g;
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
+            e[q] = *reinterpret_cast<const uint32_t *>(tb + (PK ? idx : 4u * idx));
         }
-        if (!PK && ag) {   // energy change 2m = 2(mb byte - 128) of each accepted replica
+        const uint32_t slo = __byte_perm(uw, 0u, 0x4140u) * 128u + __byte_perm(e[0], e[1], 0x5410u);
+        const uint32_t shi = __byte_perm(uw, 0u, 0x4342u) * 128u + __byte_perm(e[2], e[3], 0x5410u);
+        const uint32_t RT = prmt_sign(slo, shi, 0xFDB9u);                               // reject or tie
+        const uint32_t RS = prmt_sign(slo - 0x00010001u, shi - 0x00010001u, 0xFDB9u);   // reject
+        const uint32_t M = 0x01010101u << g;
+        acc32 |= ~RT & M;
+        acct32 |= ~RS & M;
+        if (PK) {
+            ebias[g] += ((r[g] * 2u + mq0) & ~RT) | (0x20202020u & RT);   // byte q: accepted ? 32 + m : 32
+        } else if (~RT & 0x80808080u) {   // energy change 2m = 2(mb byte - 128) of each accepted replica
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if ((ag >> (8 * q)) & 1u) atomicAdd(&Eacc[4 * g + q], 2 * ((int)((mb >> (8 * q)) & 0xFFu) - 128));
+                if (!((RT >> (8 * q)) & 1u)) atomicAdd(&Eacc[4 * g + q], 2 * ((int)((mb >> (8 * q)) & 0xFFu) - 128));
         }
+    }
+    uint32_t tie = acct32 & ~acc32;
+    if (tie) {   // rare: the low 24 bits of the uniform decide
+        const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
+        do {
+            const int bit = __ffs(tie) - 1;
+            tie &= tie - 1u;
+            const int g = bit & 7;
+            uint32_t rg = r[0];   // count byte of the replica at this bit: byte bit >> 3 of r[bit & 7]
+#pragma unroll
+            for (int j = 1; j < 8; ++j)
+                if (g == j) rg = r[j];
+            const int m = 2 * (int)((rg >> (bit & 24)) & 0xFFu) - (int)deg;
+            const uint32_t T = __ldg(&tab[m]);
+            const int rep = 4 * (bit & 7) + (bit >> 3);
+            if (sweep_tail_bits(vid, 32u * blk + rep, (uint32_t)a.k, c3, a.key0, a.key1) < (T & 0xFFFFFFu)) {
+                acc32 |= 1u << bit;
+                atomicAdd(&Eacc[rep], 2 * m);
+            }
+        } while (tie);
     }
     return acc32;
 }
@@ -821,7 +869,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     const bool act = !a.active || a.active[a.k];
     const int nsweeps = act ? a.S : 0;
     const int np = a.g.np, n = a.g.n;
-    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] decision table (see above) or thresholds by m + 128
+    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] decision table (see above)
     uint32_t *Wsm = T256 + 256;                                     // [np]
     int32_t *cls = reinterpret_cast<int32_t *>(Wsm + np);
     const int csz = (a.g.ncol + 1 + 3) & ~3;
@@ -831,18 +879,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
 
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
-    for (int i = tid; i < 256; i += NT) {
-        if (MscPackedE<NPL>::value) {
-            // words 0..63: low halves of 2^64 - threshold of m = i - 32; words 64..127: high halves
-            const int m = (i & 63) - 32;
-            const uint32_t thr = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
-            const bool always = m <= 0, never = !always && thr == 0u;
-            T256[i] = i < 64 ? ((always || never) ? 0u : 0u - thr) : (i < 128 && !never ? 0xFFFFFFFFu : 0u);
-        } else {
-            const int m = i - 128;
-            T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
-        }
-    }
+    for (int i = tid; i < 256; i += NT) T256[i] = msc_entry(i, MscPackedE<NPL>::value, tab, a.g.mmax);
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
 
     for (int lb = blockIdx.x; lb < a.nblk; lb += gridDim.x) {
@@ -950,7 +987,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
     const bool act = !a.active || a.active[a.k];
     const int nsweeps = act ? a.S : 0;
     const int np = a.g.np, n = a.g.n;
-    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] decision table (see above) or thresholds by m + 128
+    uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] decision table (see above)
     uint32_t *Wsm = T256 + 256;                                     // [np]
     int32_t *cls = reinterpret_cast<int32_t *>(Wsm + np);
     const int csz = (a.g.ncol + 1 + 3) & ~3;
@@ -962,18 +999,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
 
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
-    for (int i = tid; i < 256; i += NT) {
-        if (MscPackedE<NPL>::value) {
-            // words 0..63: low halves of 2^64 - threshold of m = i - 32; words 64..127: high halves
-            const int m = (i & 63) - 32;
-            const uint32_t thr = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
-            const bool always = m <= 0, never = !always && thr == 0u;
-            T256[i] = i < 64 ? ((always || never) ? 0u : 0u - thr) : (i < 128 && !never ? 0xFFFFFFFFu : 0u);
-        } else {
-            const int m = i - 128;
-            T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
-        }
-    }
+    for (int i = tid; i < 256; i += NT) T256[i] = msc_entry(i, MscPackedE<NPL>::value, tab, a.g.mmax);
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
 
     const int ncl = (int)(gridDim.x >> 1);

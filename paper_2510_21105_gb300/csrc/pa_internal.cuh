@@ -27,6 +27,11 @@ __host__ __device__ __forceinline__ void mul_wide(uint32_t a, uint32_t b, uint32
     hi = (uint32_t)(p >> 32);
 }
 
+// Word w (0..3) of a Philox output.
+__host__ __device__ __forceinline__ uint32_t word_of(const uint4 &v, uint32_t w) {
+    return w == 0 ? v.x : w == 1 ? v.y : w == 2 ? v.z : v.w;
+}
+
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64
 // multiplies by 0xD2511F53 / 0xCD9E8D57, high halves xored with the other
 // counter words and the key; key advanced by 0x9E3779B9 / 0xBB67AE85.
@@ -48,6 +53,29 @@ constexpr uint32_t TAG_SWEEP = 0u << 28;
 constexpr uint32_t TAG_RESAMPLE = 1u << 28;
 constexpr uint32_t TAG_NONLOCAL = 2u << 28;
 constexpr uint32_t TAG_INIT = 3u << 28;
+constexpr uint32_t TAG_TAIL = 4u << 28;
+
+// Metropolis uniform of an attempt (vertex vid, replica slot, step k, sweep
+// s): its top 8 bits are byte (slot & 3) of word ((slot >> 2) & 3) of
+// Philox(vid, slot >> 4, k, s), so one call serves 16 replicas; its low 24
+// bits are the top 24 bits of word (slot & 3) of Philox(vid, slot >> 2, k,
+// tag 4 | s). A move with threshold T (accept iff u < T) needs the low bits
+// only when the top byte of u equals that of T (probability 1/256), so they
+// are drawn on that path alone.
+static __device__ __forceinline__ uint32_t sweep_tail_bits(uint32_t vid, uint32_t slot, uint32_t k, uint32_t s,
+                                                uint32_t key0, uint32_t key1) {
+    const uint4 v = philox10(make_uint4(vid, slot >> 2, k, TAG_TAIL | s), key0, key1);
+    return word_of(v, slot & 3u) >> 8;
+}
+
+// Decision of an attempt with m >= 1 and threshold T given the top byte of
+// its uniform (c3 = TAG_SWEEP | s): u < T.
+static __device__ __forceinline__ bool accept_by_top_byte(uint32_t top, uint32_t T, uint32_t vid, uint32_t slot,
+                                                   uint32_t k, uint32_t c3, uint32_t key0, uint32_t key1) {
+    const uint32_t t8 = T >> 24;
+    if (top != t8) return top < t8;
+    return sweep_tail_bits(vid, slot, k, c3 & 0x0FFFFFFFu, key0, key1) < (T & 0xFFFFFFu);
+}
 
 constexpr int32_t EMIN_SENTINEL = 0x7F7F7F7F;  // byte-fillable "+infinity"
 constexpr int RS_CHUNK = 256;                   // slots per resampling CTA (power of two)

@@ -189,6 +189,32 @@ def test_fixed_beta_histogram_matches_boltzmann_chi_square():
     assert stat.pvalue > 1e-3, stat
 
 
+def test_sweep_uniform_is_uniform_at_full_resolution():
+    """The Metropolis uniform of an attempt takes its top byte from a Philox
+    call shared by 16 replicas and its low 24 bits from a second stream. It
+    must be uniform on [0, 2^32): P(u < T) = T / 2^32 also for thresholds
+    inside one top-byte band, where a comparison of the top byte alone (or
+    with a constant tail) is off by up to 1/256; replicas that share a call
+    draw different top bytes."""
+    from scipy.stats import chisquare
+
+    n = 1 << 21
+    verts = np.arange(n) % 7000          # distinct (vertex, replica) pairs
+    slots = np.arange(n) // 7000
+    u = oracle.sweep_uniforms(0x1234_5678_9ABC, verts, slots, 17, 3).astype(np.int64)
+    assert chisquare(np.bincount(u >> 28, minlength=16)).pvalue > 1e-3
+    sigma = math.sqrt(0.25 / n)
+    for T in (0x80000001, 0x80800000, 0x80FFFFFF):
+        assert abs(np.mean(u < T) - T / 2.0 ** 32) < 5 * sigma, hex(T)
+    # the 16 replicas of one call, and the tail stream: pairwise independent top bytes
+    v = np.arange(1 << 16)
+    top = np.stack([oracle.sweep_uniforms(9, v, np.full(v.size, r), 4, 0) >> 24 for r in range(16)])
+    for a, b in [(0, 1), (0, 4), (3, 15), (5, 6)]:
+        assert abs(np.mean(top[a] == top[b]) - 1 / 256) < 5 * math.sqrt(1 / 256 / v.size)
+    low = oracle.sweep_uniforms(9, v, np.full(v.size, 2), 4, 0) & 0xFFFFFF
+    assert chisquare(np.bincount(low >> 20, minlength=16)).pvalue > 1e-3
+
+
 def test_accept_table_is_floor_of_boltzmann_factor():
     for beta in [0.0, 0.1, 1.0, 3.7]:
         T = oracle.accept_table(beta, 40)
