@@ -422,6 +422,79 @@ int pa_resample_noalloc(const int32_t *energies, int32_t R, double beta_prev, do
                         uint64_t seed, int32_t k, int32_t *parent, int32_t *counts,
                         pa_resample_result *out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Resampling of one population split over G ranks (replica sharding across
+ * GPUs). Sec. 3 runs population annealing on one GPU; the reweighting and
+ * systematic resampling here are those of pa_anneal (weights
+ * q^(E - E_min) as FP64 products of squarings, pairwise tree sum A, integer
+ * weights t = floor(2^32 w), copies F(P + t) - F(P) with
+ * F(P) = floor((P R 2^32 + o T) / (T 2^32))), computed shard by shard so that
+ * every output equals the single-population resampling bit for bit.
+ *
+ * Layout: R = 2^a replicas (R <= 65536) over G = 2^b ranks (G <= R, G <=
+ * PA_SHARD_MAX_RANKS); rank g holds slots [g R/G, (g+1) R/G), one subtree of
+ * the pairwise weight tree. One step on rank g (the caller does the three
+ * collectives, e.g. with torch.distributed):
+ *   pa_shard_min      -> E_min,g; all-reduce min -> E_min
+ *   pa_shard_partials -> A_g, T_g (+ t and its prefix in scratch); all-gather
+ *   pa_shard_plan     -> A, T, the new slots [new_lo, new_hi) this rank's
+ *                        parents fill (contiguous: systematic resampling keeps
+ *                        parent order) and the rows sent to / received from
+ *                        every rank
+ *   pa_shard_parents  -> local parent of each of those new slots
+ *   pa_shard_gather   -> rows in new-slot order; all-to-all with the plan's
+ *                        counts; rows arrive in new-slot order.
+ * Device pointers: energies int32[n], scratch of pa_shard_scratch_bytes(n)
+ * bytes (caller-owned, kept between pa_shard_partials and pa_shard_parents),
+ * src int32[new_hi - new_lo], counts int32[n] or NULL. stream: cudaStream_t or
+ * NULL. pa_shard_plan and pa_resample_offset are host-only and need no GPU.
+ * Errors: PA_EINVAL (sizes, layout, schedule), PA_ECUDA.
+ */
+#define PA_SHARD_MAX_RANKS 64
+#define PA_SHARD_MAX_SLOTS 65536
+
+typedef struct {
+    double A;                 /* weight sum of the whole population (bitwise) */
+    uint64_t T;               /* integer weight total of the whole population */
+    uint64_t P_base;          /* integer weights of the ranks before this one */
+    int32_t new_lo, new_hi;   /* new slots filled by this rank's parents */
+    int32_t send[PA_SHARD_MAX_RANKS];   /* rows to rank h (new-slot order) */
+    int32_t recv[PA_SHARD_MAX_RANKS];   /* rows from rank h (new-slot order) */
+} pa_shard_step;
+
+size_t pa_shard_scratch_bytes(int32_t n);
+int pa_shard_min(const int32_t *energies, int32_t n, int32_t *scratch, int32_t *emin, void *stream);
+int pa_shard_partials(const int32_t *energies, int32_t n, int32_t emin, double beta_prev, double beta_k,
+                      void *scratch, double *A, uint64_t *T, void *stream);
+int pa_shard_plan(int32_t G, int32_t g, int32_t R, const double *A_all, const uint64_t *T_all, uint32_t o,
+                  pa_shard_step *out);
+int pa_shard_parents(const void *scratch, int32_t n, int32_t R, uint32_t o, const pa_shard_step *step,
+                     int32_t *src, int32_t *counts, void *stream);
+int pa_shard_gather(const int8_t *spins, const int32_t *energies, int32_t ncols, const int32_t *src, int32_t nout,
+                    int8_t *spins_out, int32_t *energies_out, void *stream);
+/* Offset word o of the resampling of step k: word 0 of Philox(0, 0, k, tag 1)
+ * keyed by the seed (host). */
+uint32_t pa_resample_offset(uint64_t seed, int32_t k);
+
+/* ---------------------------------------------------------------------------
+ * Throughput probes of the current device (no counterpart in the paper; they
+ * give the roofline denominators of the sweep, which is bound by integer
+ * issue): register-only and shared-memory-only loops, four 256-thread CTAs per
+ * SM, best of three launches timed with CUDA events on `stream` (NULL =
+ * legacy default stream). Takes a few tens of milliseconds; allocates nothing.
+ * Errors: PA_EINVAL (out NULL), PA_ECUDA.
+ */
+typedef struct {
+    double int_ops_per_s;      /* 32-bit integer instructions per second, 1:1 mix
+                                  of multiply-adds (IMAD) and three-input logic
+                                  ops (LOP3), eight independent chains a thread */
+    double philox_words_per_s; /* Philox4x32-10 output words per second */
+    double smem_bytes_per_s;   /* shared-memory load bandwidth, 16-byte loads */
+    int32_t sms;               /* multiprocessors of the device */
+} pa_peaks;
+
+int pa_probe_peaks(pa_peaks *out, void *stream);
+
 /* Text of an error code, and the detail of the last error on ctx. */
 const char *pa_strerror(int code);
 const char *pa_last_error(const pa_ctx *ctx);

@@ -26,15 +26,29 @@ _lock = threading.Lock()
 _lib = None
 
 
+_LIB_OMP = os.path.join(_HERE, "_build", "libpamc_oracle_omp.so")
+_lib_omp = None
+
+
+def _compile(out: str, extra, force: bool) -> str:
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared", *extra,
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (single-threaded, no FMA contraction)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    return _compile(_LIB, [], force)
+
+
+def build_parallel(force: bool = False) -> str:
+    """The same source built with OpenMP: replicas swept on several threads
+    between resamplings. For timing only; results equal the checking build."""
+    return _compile(_LIB_OMP, ["-fopenmp"], force)
 
 
 class OrcOpts(C.Structure):
@@ -54,36 +68,60 @@ class OrcOut(C.Structure):
                 ("best", C.c_int32 * 4), ("steps_run", C.c_int32)]
 
 
+def _declare(L):
+    """Argument and result types of the oracle's C functions."""
+    vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
+    L.orc_philox4x32_10.argtypes = [vp, vp, vp]
+    L.orc_energy.argtypes = [i32, vp, vp, vp, vp]
+    L.orc_energy.restype = i64
+    L.orc_total_weight.argtypes = [i32, vp, vp, vp]
+    L.orc_total_weight.restype = i64
+    L.orc_greedy_colour.argtypes = [i32, vp, vp, vp]
+    L.orc_greedy_colour.restype = i32
+    L.orc_accept_table.argtypes = [dbl, i32, vp]
+    L.orc_resample.argtypes = [i32, vp, dbl, C.c_uint32, vp, vp, vp, vp, vp]
+    L.orc_resample.restype = C.c_int
+    L.orc_houdayer_pair.argtypes = [i32, vp, vp, vp, vp, C.c_uint32, vp]
+    L.orc_houdayer_pair.restype = i32
+    L.orc_nlm_order.argtypes = [i32, u64, i32, vp]
+    L.orc_anneal.argtypes = [i32, vp, vp, vp, vp, i32, i32, i32, u64, C.POINTER(OrcOpts),
+                             C.POINTER(OrcOut)]
+    L.orc_anneal.restype = C.c_int
+    L.orc_step.argtypes = [i32, vp, vp, vp, i32, i32, u64, i32, dbl, dbl, i32, i32, vp, i32,
+                           vp, vp, vp, vp, vp]
+    L.orc_block_move.argtypes = [i32, vp, vp, vp, vp, vp, i32, dbl, i32, C.c_uint32, vp]
+    L.orc_block_move.restype = i32
+    L.orc_step.restype = C.c_int
+    L.orc_sweep_uniforms.argtypes = [u64, i32, vp, vp, i32, i32, vp]
+    L.orc_shard_partials.argtypes = [i32, vp, i32, dbl, C.POINTER(dbl), C.POINTER(u64), vp]
+    L.orc_systematic_count.argtypes = [u64, i32, u64, C.c_uint32]
+    L.orc_systematic_count.restype = i64
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            _lib = C.CDLL(build())
-            L = _lib
-            vp, i32, i64, u64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64, C.c_double
-            L.orc_philox4x32_10.argtypes = [vp, vp, vp]
-            L.orc_energy.argtypes = [i32, vp, vp, vp, vp]
-            L.orc_energy.restype = i64
-            L.orc_total_weight.argtypes = [i32, vp, vp, vp]
-            L.orc_total_weight.restype = i64
-            L.orc_greedy_colour.argtypes = [i32, vp, vp, vp]
-            L.orc_greedy_colour.restype = i32
-            L.orc_accept_table.argtypes = [dbl, i32, vp]
-            L.orc_resample.argtypes = [i32, vp, dbl, C.c_uint32, vp, vp, vp, vp, vp]
-            L.orc_resample.restype = C.c_int
-            L.orc_houdayer_pair.argtypes = [i32, vp, vp, vp, vp, C.c_uint32, vp]
-            L.orc_houdayer_pair.restype = i32
-            L.orc_nlm_order.argtypes = [i32, u64, i32, vp]
-            L.orc_anneal.argtypes = [i32, vp, vp, vp, vp, i32, i32, i32, u64, C.POINTER(OrcOpts),
-                                     C.POINTER(OrcOut)]
-            L.orc_anneal.restype = C.c_int
-            L.orc_step.argtypes = [i32, vp, vp, vp, i32, i32, u64, i32, dbl, dbl, i32, i32, vp, i32,
-                                   vp, vp, vp, vp, vp]
-            L.orc_block_move.argtypes = [i32, vp, vp, vp, vp, vp, i32, dbl, i32, C.c_uint32, vp]
-            L.orc_block_move.restype = i32
-            L.orc_step.restype = C.c_int
-            L.orc_sweep_uniforms.argtypes = [u64, i32, vp, vp, i32, i32, vp]
+            _lib = _declare(C.CDLL(build()))
         return _lib
+
+
+def lib_parallel(threads: int = 0):
+    """The OpenMP timing build (threads > 0 sets its thread count)."""
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            _lib_omp = _declare(C.CDLL(build_parallel()))
+            _lib_omp.orc_threads.argtypes = [C.c_int32]
+            _lib_omp.orc_threads.restype = C.c_int
+    if threads:
+        _lib_omp.orc_threads(int(threads))
+    return _lib_omp
+
+
+def parallel_threads() -> int:
+    return int(lib_parallel().orc_threads(0))
 
 
 def _p(a):
@@ -155,6 +193,21 @@ def resample(E, q: float, o: int):
     return dict(counts=counts, parent=parent, emin=emin.value, A=A.value, T=T.value)
 
 
+def shard_partials(E, emin: int, q: float):
+    """Weights of one shard with the population's E_min given: (A, T, t)
+    (``orc_shard_partials``)."""
+    E = np.ascontiguousarray(E, dtype=np.int32)
+    t = np.zeros(len(E), np.uint64)
+    A, T = C.c_double(), C.c_uint64()
+    lib().orc_shard_partials(len(E), _p(E), int(emin), float(q), C.byref(A), C.byref(T), _p(t))
+    return A.value, T.value, t
+
+
+def systematic_count(P: int, R: int, T: int, o: int) -> int:
+    """F(P) of systematic resampling (``orc_systematic_count``)."""
+    return int(lib().orc_systematic_count(int(P), int(R), int(T), int(o)))
+
+
 def houdayer_pair(rp, col, xa, xb, u: int):
     rp, col, _ = _graph_arrays(rp, col, None)
     xa = np.array(xa, dtype=np.int8)
@@ -212,8 +265,9 @@ def anneal(rp, col, w, betas, R: int, S: int, seed: int, *, K: int | None = None
            nlm_period: int = 0, adaptive: int = 0, rho: float = 0.5, adapt_J: int = 8,
            adapt_dbeta_max: float = 0.05, beta_max: float = 0.0, record_counts: bool = False,
            nlm_kind: int = 0, nlm_block: int = 1, acc_lo: float = 0.0, acc_hi: float = 1.0,
-           reheat_after: int = 0, reheat_back: int = 0):
-    """Run the oracle PAMC (see ``orc_anneal`` in pamc_oracle.c)."""
+           reheat_after: int = 0, reheat_back: int = 0, parallel: bool = False):
+    """Run the oracle PAMC (see ``orc_anneal`` in pamc_oracle.c). parallel:
+    the OpenMP timing build (same results)."""
     rp, col, w = _graph_arrays(rp, col, w)
     n = len(rp) - 1
     if adaptive:
@@ -238,7 +292,8 @@ def anneal(rp, col, w, betas, R: int, S: int, seed: int, *, K: int | None = None
     for name, a in arr.items():
         setattr(out, name, a.ctypes.data)
     out.step_counts = counts.ctypes.data if counts is not None else None
-    rc = lib().orc_anneal(n, _p(rp), _p(col), _p(w), _p(b), int(K), int(R), int(S), int(seed),
+    L = lib_parallel() if parallel else lib()
+    rc = L.orc_anneal(n, _p(rp), _p(col), _p(w), _p(b), int(K), int(R), int(S), int(seed),
                           C.byref(opts), C.byref(out))
     if rc != 0:
         raise ValueError(f"orc_anneal rejected its arguments (rc={rc})")

@@ -229,6 +229,31 @@ static int64_t systematic_count(uint64_t P, int32_t R, uint64_t T, uint32_t o)
  *   parent r gets copies into new slots [F(P_r), F(P_r + t_r)).
  * Outputs: counts[r] (may be NULL), parent[s] for every new slot s (may be
  * NULL), E_min, A, T. Returns 0, or -1 if R < 1 or q is not in (0, 1]. */
+/* One shard of a population split over ranks (for the sharded-resampling
+ * tests): with the population's E_min given, the weights of the shard's n
+ * slots, their pairwise tree sum (zero-padded to a power of two), the integer
+ * weights t[n] and their total. Same arithmetic as orc_resample. */
+void orc_shard_partials(int32_t n, const int32_t *E, int32_t emin, double q, double *A, uint64_t *T,
+                        uint64_t *t)
+{
+    double *w = (double *)malloc((size_t)n * sizeof(double));
+    uint64_t tot = 0;
+    for (int32_t r = 0; r < n; ++r) {
+        w[r] = power_sq_mul(q, (uint32_t)((int64_t)E[r] - emin));
+        t[r] = (uint64_t)floor(ldexp(w[r], 32));
+        tot += t[r];
+    }
+    *A = tree_sum(w, n);
+    *T = tot;
+    free(w);
+}
+
+/* Systematic resampling boundary F(P) (see orc_resample). */
+int64_t orc_systematic_count(uint64_t P, int32_t R, uint64_t T, uint32_t o)
+{
+    return systematic_count(P, R, T, o);
+}
+
 int orc_resample(int32_t R, const int32_t *E, double q, uint32_t o,
                  int32_t *counts, int32_t *parent,
                  int32_t *emin_out, double *A_out, uint64_t *T_out)
@@ -510,6 +535,22 @@ static uint32_t sweep_uniform(uint64_t seed, int32_t i, int32_t slot, int32_t k,
     return (top << 24) | (tail >> 8);
 }
 
+/* Threads of the timing build (OpenMP); 1 in the checking build. */
+#ifdef _OPENMP
+#include <omp.h>
+int orc_threads(int32_t want)
+{
+    if (want > 0) omp_set_num_threads(want);
+    return omp_get_max_threads();
+}
+#else
+int orc_threads(int32_t want)
+{
+    (void)want;
+    return 1;
+}
+#endif
+
 /* Uniforms of n attempts (vertex i[t], replica slot[t]) at step k, sweep s,
  * for the tests. */
 void orc_sweep_uniforms(uint64_t seed, int32_t n, const int32_t *i, const int32_t *slot, int32_t k,
@@ -774,6 +815,10 @@ int orc_anneal(int32_t n, const int64_t *rp, const int32_t *col, const int8_t *w
         step_min = 0x7FFFFFFF;
         for (int32_t s = 0; s < S; ++s) {
             int32_t sweep_min = 0x7FFFFFFF;
+            /* Replicas are independent between resamplings, so the timing
+             * build (-fopenmp) may sweep them on several threads; the result,
+             * an integer sum and per-replica state, does not depend on it. */
+#pragma omp parallel for reduction(+ : acc) schedule(dynamic, 4)
             for (int32_t r = 0; r < R; ++r)
                 acc += sweep_replica(&g, pop + (size_t)r * n, &E[r], T, seed, r, k, s);
             for (int32_t r = 0; r < R; ++r) {

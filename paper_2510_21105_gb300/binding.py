@@ -53,6 +53,16 @@ class pa_step_arrays(C.Structure):
                  "nlm_flips", "jsel", "counts", "t_ms")]
 
 
+class pa_peaks(C.Structure):
+    _fields_ = [("int_ops_per_s", C.c_double), ("philox_words_per_s", C.c_double),
+                ("smem_bytes_per_s", C.c_double), ("sms", C.c_int32)]
+
+
+class pa_shard_step(C.Structure):
+    _fields_ = [("A", C.c_double), ("T", C.c_uint64), ("P_base", C.c_uint64), ("new_lo", C.c_int32),
+                ("new_hi", C.c_int32), ("send", C.c_int32 * 64), ("recv", C.c_int32 * 64)]
+
+
 class pa_job(C.Structure):
     _fields_ = [("ctx", C.c_void_p), ("betas", C.c_void_p), ("K", C.c_int32), ("R", C.c_int32),
                 ("sweeps", C.c_int32), ("seed", C.c_uint64), ("opts", pa_anneal_opts)]
@@ -134,6 +144,14 @@ def lib():
                 "pa_server_result": ([vp, u64, C.POINTER(pa_response), vp], C.c_int),
                 "pa_server_stats": ([vp, C.POINTER(pa_server_stats_t)], C.c_int),
                 "pa_server_release": ([vp, u64], C.c_int),
+                "pa_probe_peaks": ([C.POINTER(pa_peaks), vp], C.c_int),
+                "pa_shard_scratch_bytes": ([i32], C.c_size_t),
+                "pa_shard_min": ([vp, i32, vp, C.POINTER(i32), vp], C.c_int),
+                "pa_shard_partials": ([vp, i32, i32, dbl, dbl, vp, C.POINTER(dbl), C.POINTER(u64), vp], C.c_int),
+                "pa_shard_plan": ([i32, i32, i32, vp, vp, C.c_uint32, C.POINTER(pa_shard_step)], C.c_int),
+                "pa_shard_parents": ([vp, i32, i32, C.c_uint32, C.POINTER(pa_shard_step), vp, vp, vp], C.c_int),
+                "pa_shard_gather": ([vp, vp, i32, vp, i32, vp, vp, vp], C.c_int),
+                "pa_resample_offset": ([u64, i32], C.c_uint32),
                 "pa_server_hold": ([vp, u64, i32], C.c_int),
                 "pa_server_stop": ([vp], C.c_int),
             }
@@ -153,7 +171,8 @@ def exported_symbols():
             "pa_step_stats", "pa_tables", "pa_colouring", "pa_set_allocator", "pa_run_info",
             "pa_resample_noalloc", "pa_batch_anneal", "pa_server_start", "pa_server_submit",
             "pa_server_poll", "pa_server_result", "pa_server_stats", "pa_server_stop",
-            "pa_server_release", "pa_server_hold"]
+            "pa_server_release", "pa_server_hold", "pa_probe_peaks", "pa_shard_scratch_bytes", "pa_shard_min",
+            "pa_shard_partials", "pa_shard_plan", "pa_shard_parents", "pa_shard_gather", "pa_resample_offset"]
 
 
 def strerror(code: int) -> str:
@@ -453,6 +472,14 @@ def use_torch_allocator(enable: bool = True):
 
     _alloc_refs = (ALLOC_FN(_alloc), FREE_FN(_free))
     lib().pa_set_allocator(_alloc_refs[0], _alloc_refs[1], None)
+
+
+def probe_peaks(stream=None) -> dict:
+    """Integer, Philox and shared-memory throughput of the current device
+    (pa_probe_peaks), the roofline denominators of the sweep."""
+    p = pa_peaks()
+    _check(lib().pa_probe_peaks(C.byref(p), stream), "pa_probe_peaks")
+    return {name: getattr(p, name) for name, _ in pa_peaks._fields_}
 
 
 def current_stream_handle():

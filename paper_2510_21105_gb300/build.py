@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpa.so")
-SOURCES = ["pa_api.cu", "k_sweep.cu", "k_resample.cu", "k_moves.cu", "pa_noalloc.cu", "pa_server.cu"]
+SOURCES = ["pa_api.cu", "k_sweep.cu", "k_resample.cu", "k_moves.cu", "pa_noalloc.cu", "pa_server.cu", "pa_probe.cu", "pa_shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

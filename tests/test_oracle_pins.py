@@ -215,6 +215,20 @@ def test_sweep_uniform_is_uniform_at_full_resolution():
     assert chisquare(np.bincount(low >> 20, minlength=16)).pvalue > 1e-3
 
 
+def test_parallel_timing_build_equals_checking_build():
+    """The OpenMP build (replicas swept on several threads, used only to time
+    the oracle on all host cores) gives the single-thread results bit for bit."""
+    g = wl.gnm(500, 3000, seed=3)
+    betas = wl.linear_betas(0.1, 3.0, 12)
+    a = oracle.anneal(g.rp, g.col, g.w, betas, R=48, S=3, seed=5, nlm_period=4, record_counts=True)
+    oracle.lib_parallel(4)
+    p = oracle.anneal(g.rp, g.col, g.w, betas, R=48, S=3, seed=5, nlm_period=4, record_counts=True, parallel=True)
+    assert np.array_equal(a.spins, p.spins) and np.array_equal(a.E, p.E)
+    assert np.array_equal(a.step_accepts, p.step_accepts) and np.array_equal(a.step_counts, p.step_counts)
+    assert np.array_equal(a.step_A.view(np.uint64), p.step_A.view(np.uint64))
+    assert (a.best_E, a.best_step, a.best_sweep, a.best_slot) == (p.best_E, p.best_step, p.best_sweep, p.best_slot)
+
+
 def test_accept_table_is_floor_of_boltzmann_factor():
     for beta in [0.0, 0.1, 1.0, 3.7]:
         T = oracle.accept_table(beta, 40)
