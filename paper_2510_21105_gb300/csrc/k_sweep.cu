@@ -724,6 +724,30 @@ __device__ __forceinline__ void philox_from_shared2(const PhiloxShared &p, uint3
 // change of every accepted flip, either in the lane's packed counters ebias
 // (MscPackedE) or by a shared atomic on Eacc (local or a cluster peer's shared
 // memory). Returns the mask of accepted replicas.
+// Adds four bonds to the bit-sliced counters pl (one counter per replica):
+// bit r of d_j = x ^ w_j is 1 iff bond j contributes +1 to m_r. Carry-save
+// adders: d0 + d1 = s01 + 2 c01, d0 + .. + d3 = s + 2 (c01 + c23 + cs).
+template <int NPL>
+__device__ __forceinline__ void msc_csa4(uint32_t (&pl)[NPL], uint32_t x, uint32_t w0, uint32_t w1, uint32_t w2,
+                                         uint32_t w3) {
+    const uint32_t s01 = w0 ^ w1, c01 = (x ^ w0) & (x ^ w1);
+    const uint32_t s23 = w2 ^ w3, c23 = (x ^ w2) & (x ^ w3);
+    const uint32_t s = s01 ^ s23, cs = s01 & s23;
+    const uint32_t t = pl[0] & s;
+    pl[0] ^= s;
+    const uint32_t u1 = pl[1] ^ c01 ^ c23, k1 = (pl[1] & c01) | (c23 & (pl[1] | c01));
+    const uint32_t k2 = (u1 & cs) | (t & (u1 | cs));
+    pl[1] = u1 ^ cs ^ t;
+    uint32_t k = (pl[2] & k1) | (k2 & (pl[2] | k1));
+    pl[2] ^= k1 ^ k2;
+#pragma unroll
+    for (int b = 3; b < NPL; ++b) {
+        const uint32_t carry = pl[b] & k;
+        pl[b] ^= k;
+        k = carry;
+    }
+}
+
 // Entry i of the decision table: E(m) in both 16-bit halves, m = i - 32 for
 // counts of |m| <= 31 (byte offset 4m + 128), else m = i - 128 (word index).
 __device__ __forceinline__ uint32_t msc_entry(int i, bool pk, const uint32_t *tab, int mmax) {
@@ -740,49 +764,54 @@ template <int NPL, bool WEIGHTED>
 __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t *Wsm, const uint32_t *T256, int p,
                                              uint32_t x, uint32_t c3, int blk, int32_t *Eacc,
                                              uint32_t (&ebias)[8]) {
-    const uint32_t e0 = __ldg(&a.g.rp[p]), e1 = __ldg(&a.g.rp[p + 1]);
     const uint32_t vid = __ldg(&a.g.vid[p]);
     uint32_t pl[NPL];
 #pragma unroll
     for (int b = 0; b < NPL; ++b) pl[b] = 0u;
-    uint32_t e = e0;
-    for (; e + 4 <= e1; e += 4) {   // four bonds per step through carry-save adders
-        uint32_t w0 = Wsm[__ldg(&a.g.col[e])], w1 = Wsm[__ldg(&a.g.col[e + 1])];
-        uint32_t w2 = Wsm[__ldg(&a.g.col[e + 2])], w3 = Wsm[__ldg(&a.g.col[e + 3])];
-        if (WEIGHTED) {
-            if (__ldg(&a.g.wt[e]) < 0) w0 = ~w0;
-            if (__ldg(&a.g.wt[e + 1]) < 0) w1 = ~w1;
-            if (__ldg(&a.g.wt[e + 2]) < 0) w2 = ~w2;
-            if (__ldg(&a.g.wt[e + 3]) < 0) w3 = ~w3;
-        }
-        const uint32_t s01 = w0 ^ w1, c01 = (x ^ w0) & (x ^ w1);   // d0 + d1 = s01 + 2 c01
-        const uint32_t s23 = w2 ^ w3, c23 = (x ^ w2) & (x ^ w3);
-        const uint32_t s = s01 ^ s23, cs = s01 & s23;              // d0 + .. + d3 = s + 2 (c01 + c23 + cs)
-        const uint32_t t = pl[0] & s;
-        pl[0] ^= s;
-        const uint32_t u1 = pl[1] ^ c01 ^ c23, k1 = (pl[1] & c01) | (c23 & (pl[1] | c01));
-        const uint32_t k2 = (u1 & cs) | (t & (u1 | cs));
-        pl[1] = u1 ^ cs ^ t;
-        uint32_t k = (pl[2] & k1) | (k2 & (pl[2] | k1));
-        pl[2] ^= k1 ^ k2;
+    uint32_t deg;
+    if (a.g.mcol) {
+        // Rows padded to whole 4-bond steps, entries = byte offsets of the
+        // neighbours' words: one 8-byte load per step, no single-bond tail.
+        const uint32_t h0 = __ldg(&a.g.mrp[p]), h1 = __ldg(&a.g.mrp[p + 1]);
+        deg = h0 & 0xFFu;
+        const unsigned char *Wb = reinterpret_cast<const unsigned char *>(Wsm);
+        for (uint32_t q = h0 >> 8; q < (h1 >> 8); ++q) {
+            const uint2 v = __ldg(&a.g.mcol[q]);
+            const uint32_t o[4] = {v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16};
+            uint32_t w[4];
 #pragma unroll
-        for (int b = 3; b < NPL; ++b) {
-            const uint32_t carry = pl[b] & k;
-            pl[b] ^= k;
-            k = carry;
+            for (int j = 0; j < 4; ++j) {
+                w[j] = *reinterpret_cast<const uint32_t *>(Wb + (WEIGHTED ? (o[j] & ~3u) : o[j]));
+                if (WEIGHTED && (o[j] & 1u)) w[j] = ~w[j];
+            }
+            msc_csa4<NPL>(pl, x, w[0], w[1], w[2], w[3]);
+        }
+    } else {
+        const uint32_t e0 = __ldg(&a.g.rp[p]), e1 = __ldg(&a.g.rp[p + 1]);
+        deg = e1 - e0;
+        uint32_t e = e0;
+        for (; e + 4 <= e1; e += 4) {   // four bonds per step through carry-save adders
+            uint32_t w0 = Wsm[__ldg(&a.g.col[e])], w1 = Wsm[__ldg(&a.g.col[e + 1])];
+            uint32_t w2 = Wsm[__ldg(&a.g.col[e + 2])], w3 = Wsm[__ldg(&a.g.col[e + 3])];
+            if (WEIGHTED) {
+                if (__ldg(&a.g.wt[e]) < 0) w0 = ~w0;
+                if (__ldg(&a.g.wt[e + 1]) < 0) w1 = ~w1;
+                if (__ldg(&a.g.wt[e + 2]) < 0) w2 = ~w2;
+                if (__ldg(&a.g.wt[e + 3]) < 0) w3 = ~w3;
+            }
+            msc_csa4<NPL>(pl, x, w0, w1, w2, w3);
+        }
+        for (; e < e1; ++e) {
+            uint32_t d = x ^ Wsm[__ldg(&a.g.col[e])];
+            if (WEIGHTED && __ldg(&a.g.wt[e]) < 0) d = ~d;
+#pragma unroll
+            for (int b = 0; b < NPL; ++b) {   // ripple-carry add of one bit per replica
+                const uint32_t carry = pl[b] & d;
+                pl[b] ^= d;
+                d = carry;
+            }
         }
     }
-    for (; e < e1; ++e) {
-        uint32_t d = x ^ Wsm[__ldg(&a.g.col[e])];
-        if (WEIGHTED && __ldg(&a.g.wt[e]) < 0) d = ~d;
-#pragma unroll
-        for (int b = 0; b < NPL; ++b) {   // ripple-carry add of one bit per replica
-            const uint32_t carry = pl[b] & d;
-            pl[b] ^= d;
-            d = carry;
-        }
-    }
-    const uint32_t deg = e1 - e0;
     constexpr bool PK = MscPackedE<NPL>::value;
     const uint32_t base = PK ? 128u - 4u * deg : 128u - deg;   // mb byte = 4m + 128 (PK, deg <= 31) or m + 128
     // Both Philox calls of the item (slots 32 blk .. +15 and +16 .. +31).

@@ -146,8 +146,8 @@ struct pa_ctx {
     std::vector<uint32_t> rp_p;         // position-order CSR
     std::vector<uint16_t> col_p;
     std::vector<int8_t> w_p;
-    DevBuf d_rp, d_col, d_w, d_vid, d_cls, d_pos, d_parity, d_prp, d_pcol;
-    bool packed_ok = false;
+    DevBuf d_rp, d_col, d_w, d_vid, d_cls, d_pos, d_parity, d_prp, d_pcol, d_mrp, d_mcol;
+    bool packed_ok = false, msc_rows = false;
     RunState run;
     std::string err;
     int64_t h2d = 0, d2h = 0;
@@ -167,6 +167,8 @@ struct pa_ctx {
         g.prp = d_prp.as<uint32_t>();
         g.pcol = d_pcol.as<uint2>();
         g.packed_ok = packed_ok ? 1 : 0;
+        g.mrp = msc_rows ? d_mrp.as<uint32_t>() : nullptr;
+        g.mcol = msc_rows ? d_mcol.as<uint2>() : nullptr;
         return g;
     }
 };
@@ -463,6 +465,30 @@ int pa_create(pa_ctx **out, int32_t n, const uint32_t *row_ptr, const uint16_t *
         }
         e1 = copy(c, c->d_prp.p, prp.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice);
         if (e1 == cudaSuccess) e1 = copy(c, c->d_pcol.p, pcol.data(), 2 * pcol.size(), cudaMemcpyHostToDevice);
+    }
+    c->msc_rows = c->np <= 16384 && c->maxdeg <= 127;
+    if (e1 == cudaSuccess && c->msc_rows) {
+        std::vector<uint32_t> mrp(n + 1, 0u);
+        uint32_t units = 0;
+        for (int32_t p = 0; p < n; ++p) {
+            const uint32_t d = c->rp_p[p + 1] - c->rp_p[p];
+            mrp[p] = units << 8 | d;
+            units += (d + 3) / 4;
+        }
+        mrp[n] = units << 8;
+        std::vector<uint16_t> mcol((size_t)units * 4 + 4);
+        for (int32_t p = 0; p < n; ++p) {
+            size_t o = (size_t)(mrp[p] >> 8) * 4;
+            for (uint32_t e = c->rp_p[p]; e < c->rp_p[p + 1]; ++e, ++o)
+                mcol[o] = (uint16_t)(4u * c->col_p[e] | (c->w_p[e] < 0 ? 1u : 0u));
+            for (; o < (size_t)(mrp[p + 1] >> 8) * 4; ++o) mcol[o] = (uint16_t)(4u * (uint32_t)p);
+        }
+        if (!c->d_mrp.alloc(4 * (size_t)(n + 1)) || !c->d_mcol.alloc(2 * mcol.size())) {
+            delete c;
+            return PA_ENOMEM;
+        }
+        e1 = copy(c, c->d_mrp.p, mrp.data(), 4 * (size_t)(n + 1), cudaMemcpyHostToDevice);
+        if (e1 == cudaSuccess) e1 = copy(c, c->d_mcol.p, mcol.data(), 2 * mcol.size(), cudaMemcpyHostToDevice);
     }
     if (e1 == cudaSuccess) {
         std::vector<uint32_t> par((c->np + 31) / 32, 0u);

@@ -95,6 +95,13 @@ struct GraphDev {
     const uint32_t *prp;     // [n+1] row starts in units of 4 entries
     const uint2 *pcol;       // [prp[n]] four 16-bit entries each
     int32_t packed_ok;       // the padded encoding exists (np + 32 <= 32768)
+    // Rows for the multi-spin-coded kernels (np <= 16384, degree <= 127), padded
+    // to multiples of 4 entries: entry = 4 * neighbour position (the byte
+    // offset of its word) | 1 if the weight is -1; padding entries point at the
+    // row's own position (its word XOR itself counts nothing). mrp[p] = (row
+    // start in units of 4 entries) << 8 | degree. nullptr when absent.
+    const uint32_t *mrp;     // [n+1]
+    const uint2 *mcol;       // [mrp[n] >> 8]
 };
 
 struct SweepArgs {
