@@ -43,15 +43,25 @@ def parse():
     p.add_argument("--steps", type=int, default=2)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="anneal", choices=["anneal", "batch", "serve"],
-                   help="anneal: the headline line; batch / serve: the batched and served workloads")
+    p.add_argument("--mode", default="anneal", choices=["anneal", "batch", "serve", "oracle"],
+                   help="anneal: the headline line; batch / serve: the batched and served workloads; "
+                        "oracle: the oracle timing plan on the host cores")
+    p.add_argument("--oracle-steps", type=int, default=100,
+                   help="oracle mode: steps of the single-thread G63-shaped run")
     p.add_argument("--instances", type=int, default=64)
     p.add_argument("--streams", type=int, default=32, help="batch mode: concurrent streams")
+    p.add_argument("--use-graph", type=int, default=0,
+                   help="batched arm: 1 = capture the batch into one CUDA graph; 0 (default) enqueues it on the "
+                        "streams directly, measured faster once graph construction is timed")
+    p.add_argument("--slots", type=int, default=16, help="serve mode: concurrently running requests")
+    p.add_argument("--tick", type=int, default=8, help="serve mode: temperature steps per tick")
     p.add_argument("--serve-seconds", type=float, default=3.0, help="arrival window of the served trace")
     p.add_argument("--rate", type=float, default=20.0, help="mean arrivals per second")
     p.add_argument("--config", default="g63like")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-batch-serve", action="store_true",
+                   help="skip the batched and served measurements of the default line")
     p.add_argument("--field-bits", type=int, default=0, help="0 = auto layout")
     p.add_argument("--threads", type=int, default=0, help="threads per sweep CTA (0 = auto)")
     p.add_argument("--variant", type=int, default=2, help="0 int8 layouts, 1 multi-spin coded, 2 auto")
@@ -122,29 +132,72 @@ class ClockSampler:
 
 
 # ------------------------------------------------------ reference (oracle) ---
-def cpu_oracle_sample(cfg_name: str, seconds: float):
+def cpu_oracle_sample(cfg_name: str, seconds: float, threads: int = 1, R: int = 16):
     """Time the oracle on a bounded sample of the benchmark workload: the same
-    graph and schedule, a few replicas, the first temperature steps."""
+    graph and schedule, R replicas, the first temperature steps. threads > 1
+    uses the oracle's OpenMP timing build (replicas swept on that many host
+    threads between resamplings; same results)."""
     import oracle
     from paper_2510_21105_gb300 import workloads as wl
 
     c = wl.CONFIGS[cfg_name]
     g = c["graph"]()
     betas = wl.linear_betas(*c["beta"], c["K"])
-    R = 16
+    par = threads > 1
+    if par:
+        oracle.lib_parallel(threads)
     # calibrate: 2 steps, then scale the step count to the time budget
     t0 = time.perf_counter()
-    oracle.anneal(g.rp, g.col, g.w, betas[:2], R=R, S=c["S"], seed=c["seed"])
+    oracle.anneal(g.rp, g.col, g.w, betas[:2], R=R, S=c["S"], seed=c["seed"], parallel=par)
     per_step = (time.perf_counter() - t0) / 2
     K = int(max(2, min(c["K"], seconds / max(per_step, 1e-6))))
     t0 = time.perf_counter()
     oracle.anneal(g.rp, g.col, g.w, betas[:K], R=R, S=c["S"], seed=c["seed"],
-                  nlm_period=c["nlm_period"])
+                  nlm_period=c["nlm_period"], parallel=par)
     dt = time.perf_counter() - t0
     attempts = g.n * R * c["S"] * K
-    return {"value": attempts / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": attempts / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{cfg_name} graph, R={R}, first {K} of {c['K']} steps x {c['S']} sweeps "
-                      f"({attempts:.3g} attempts, {dt:.1f} s, single thread)"}
+                      f"({attempts:.3g} attempts, {dt:.1f} s, "
+                      + ("single thread" if not par else f"{threads} threads, OpenMP over replicas") + ")"}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_plan(args):
+    """The oracle timing plan of the measurement: the small random-graph
+    workload (N=800, R=256, K=100, S=4) in full, and the G63-shaped graph with
+    R=256 over all K=1000 steps, on one host core and on all of them (the
+    single-thread run of the latter is bounded to --oracle-steps steps)."""
+    import oracle
+    from paper_2510_21105_gb300 import workloads as wl
+
+    cores = host_cores()
+    out = {"mode": "oracle", "unit": UNIT, "nproc": cores, "runs": []}
+    for name, R, K1 in (("gnp800", 256, None), ("g63like", 256, args.oracle_steps)):
+        c = wl.CONFIGS[name]
+        g = c["graph"]()
+        betas = wl.linear_betas(*c["beta"], c["K"])
+        for threads in (1, cores):
+            K = c["K"] if (threads > 1 or K1 is None) else min(K1, c["K"])
+            if threads > 1:
+                oracle.lib_parallel(threads)
+            t0 = time.perf_counter()
+            res = oracle.anneal(g.rp, g.col, g.w, betas[:K], R=R, S=c["S"], seed=c["seed"],
+                                nlm_period=c["nlm_period"], parallel=threads > 1)
+            dt = time.perf_counter() - t0
+            att = g.n * R * c["S"] * K
+            out["runs"].append({"workload": name, "R": R, "steps": K, "of_steps": c["K"], "threads": threads,
+                                "attempts": att, "seconds": dt, "attempts_per_s": att / dt,
+                                "best_cut": int((oracle.total_weight(g.rp, g.col, g.w) - res.best_E) // 2)})
+            print(json.dumps(out["runs"][-1]), flush=True)
+    print(json.dumps(out), flush=True)
+    return 0
 
 
 def run_reference(args, rank, world):
@@ -172,44 +225,88 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ ours ---
-# DRAM bytes (read + write) of one sweep launch on this workload, from one ncu
-# capture of the kernel; reported only while the captured kernel is the one
-# that runs. The multi-spin-coded kernels changed after their last capture, so
-# they report none.
-SWEEP_TRAFFIC = {("k_sweep_packed", 128): 334.719744e6 + 289.454080e6}
-OPS_PER_ATTEMPT = 20.0   # a quarter Philox4x32-10 block (15) + decision (4) + flip updates (~1)
-INT_LANES_PER_SM = 128   # ALU pipe (LOP3/IADD3) 64 + FMA pipe (IMAD) 64
+# DRAM bytes (read + write) of one sweep step on this workload (the head and
+# tail launches of the multi-spin-coded sweep, or the one launch of another
+# layout), from one ncu capture, with the SHA-256 prefix of the sweep source it
+# was taken on: reported only while that source is the one that runs.
+SWEEP_TRAFFIC = {}
+SWEEP_SRC = os.path.join(ROOT, "paper_2510_21105_gb300", "csrc", "k_sweep.cu")
+INT_LANES_PER_SM = 128   # ALU pipe 64 + FMA pipe 64 integer lanes per SM and clock (unit counts)
+SMEM_BYTES_PER_SM = 128  # shared-memory bytes per SM and clock (32 banks x 4 B)
+
+
+def sweep_source_sha() -> str:
+    import hashlib
+
+    with open(SWEEP_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def msc_ops_per_attempt(mean_degree: float) -> float:
+    """Algorithmic integer instructions of one multi-spin-coded attempt: one
+    item (one position of a 32-replica word) divided by its 32 attempts.
+      bond counting   18 three-input logic ops per 4 bonds (carry-save adders)
+      count bytes     8 x 8 bit transpose in every byte lane: 12 swaps x 4 ops
+      uniforms        2 Philox4x32-10 calls x 10 rounds x (2 widening
+                      multiplies + 2 three-input xors)
+      decisions       per 4-replica group: 4 index extracts, 2 entry merges,
+                      2 uniform spreads, 2 multiply-adds, 2 subtracts, 2 sign
+                      permutes, 2 mask merges
+      energies        per group: table index, count byte, masked select, add
+    Loads, addressing, loop control, barriers and the row packing at load and
+    store are not counted."""
+    per_item = 4.5 * mean_degree + 12 * 4 + 2 * 10 * 4 + 8 * 16 + 8 * 4
+    return per_item / 32.0
+
+
+def packed_ops_per_attempt(mean_degree: float, accept_rate: float) -> float:
+    """4-replica layouts: one Philox call per 4 attempts (40 ops), the
+    decision (5) and the field updates of an accepted flip (2 per bond)."""
+    return 40.0 / 4 + 5.0 + accept_rate * 2.0 * mean_degree
 
 
 def smem_bytes_per_attempt(kernel, mean_degree, accept_rate):
-    """Algorithmic shared-memory bytes of one attempt. Multi-spin coded: per
-    (position, 32-replica word) item the neighbours' words and the item's own
-    word read and written, spread over 32 attempts, plus the two 4-byte halves
-    of the decision-table entry of each attempt. 4-replica layouts: the
-    spin/field byte read and written and the threshold word, plus the
-    neighbours' field bytes read and written on an accepted flip."""
+    """Algorithmic shared-memory bytes of one attempt. Multi-spin coded (the
+    measurement plan's figure): (8 + 6 d) / 32, the item's own word read and
+    written plus a 4-byte neighbour word and its 2-byte index per bond, over
+    32 attempts. 4-replica layouts: the spin/field byte read and written and
+    the threshold word, plus the neighbours' field bytes read and written on
+    an accepted flip."""
     if kernel[0].startswith("k_sweep_msc"):
-        return (4.0 * mean_degree + 8.0) / 32.0 + 8.0
+        return (8.0 + 6.0 * mean_degree) / 32.0
     return 2.0 + 4.0 + accept_rate * 2.0 * mean_degree
 
 
-def sweep_roofline(stats, attempts_per_launch, peaks, kernel, mean_degree, accept_rate):
-    """Roofline of the sweep kernel (dominant kernel): integer-issue bound."""
+def sweep_roofline(stats, attempts_per_launch, probe, clk_mhz, kernel, mean_degree, accept_rate, sms=SMS):
+    """Roofline of the sweep (the dominant kernel): integer-issue bound.
+    probe: pa_probe_peaks of the device (measured peaks) or None."""
     launches = max(stats["sweep_launches"], 1)
     t = stats["sweep_ms"] / launches / 1e3
     if t <= 0:
         return None
-    achieved = attempts_per_launch * OPS_PER_ATTEMPT / t / 1e12
-    clk = peaks.get("sm_max_mhz", 2070.0)
-    peak = SMS * INT_LANES_PER_SM * clk * 1e6 / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak, "traffic": SWEEP_TRAFFIC.get(kernel),
+    aps = attempts_per_launch / t
+    msc = kernel[0].startswith("k_sweep_msc")
+    ops = msc_ops_per_attempt(mean_degree) if msc else packed_ops_per_attempt(mean_degree, accept_rate)
+    achieved = aps * ops / 1e12
+    derived = sms * INT_LANES_PER_SM * clk_mhz * 1e6 / 1e12
+    peak = probe["int_ops_per_s"] / 1e12 if probe else derived
+    sbpa = smem_bytes_per_attempt(kernel, mean_degree, accept_rate)
+    smem_derived = sms * SMEM_BYTES_PER_SM * clk_mhz * 1e6
+    smem_peak = probe["smem_bytes_per_s"] if probe else smem_derived
+    traffic = SWEEP_TRAFFIC.get(kernel[0])
+    if traffic and traffic[1] != sweep_source_sha():
+        traffic = None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s", "frac": achieved / peak,
+            "traffic": traffic[0] if traffic else None,
             "kernel": f"{kernel[0]}<{kernel[1]} threads>", "avg_launch_ms": t * 1e3,
-            "attempts_per_s_in_kernel": attempts_per_launch / t,
-            "peak_source": f"derived: {SMS} SMs x {INT_LANES_PER_SM} integer lanes x {clk:.0f} MHz",
-            "smem_bytes_per_attempt": smem_bytes_per_attempt(kernel, mean_degree, accept_rate),
-            "smem_frac": attempts_per_launch * smem_bytes_per_attempt(kernel, mean_degree, accept_rate) / t
-                         / (SMS * 128 * clk * 1e6)}
+            "attempts_per_s_in_kernel": aps, "ops_per_attempt": ops,
+            "peak_source": ("measured on this GPU by pa_probe_peaks (1:1 IMAD + LOP3 integer instructions)"
+                            if probe else f"derived: {sms} SMs x {INT_LANES_PER_SM} integer lanes x {clk_mhz:.0f} MHz"),
+            "peak_derived": derived, "frac_vs_derived": achieved / derived,
+            "smem_bytes_per_attempt": sbpa, "smem_frac": aps * sbpa / smem_peak,
+            "smem_frac_vs_derived": aps * sbpa / smem_derived,
+            "smem_target_met": aps * sbpa / smem_peak >= 0.5,
+            "philox_frac": (aps * (0.25 if msc else 1.0) / probe["philox_words_per_s"]) if probe else None}
 
 
 def max_over_ranks(x: float, dist, device: str = "cpu") -> float:
@@ -277,6 +374,7 @@ def run_ours(args, rank, world, dist):
                   16: "int8 spin + int16 field"}[fb]
         kernel = ("k_sweep_packed" if fb == 7 else "k_sweep", args.threads or (128 if fb == 7 else 512))
     peaks, peaks_src = load_peaks()
+    probe = B.probe_peaks(sh)   # integer, Philox and shared-memory peaks of this GPU (a few ms)
     # timed region: device-resident inputs, K anneals
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     stats_acc = {"sweep_ms": 0.0, "sweep_launches": 0, "kernel_launches": 0}
@@ -301,7 +399,9 @@ def run_ours(args, rank, world, dist):
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = aggregate_value(attempts, world, ms_max)
     clocks = clk.summary()
-    roof = sweep_roofline(stats_acc, g.n * R * S, peaks, kernel, 2.0 * g.m / g.n, acc_rate)
+    clk_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    roof = sweep_roofline(stats_acc, g.n * R * S, probe, clk_mhz, kernel, 2.0 * g.m / g.n, acc_rate,
+                          sms=probe["sms"])
     ann.close()
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the region
@@ -342,6 +442,19 @@ def run_ours(args, rank, world, dist):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = cpu_oracle_sample(args.config, args.cpu_seconds)
+        cores = host_cores()
+        cpu["nproc"] = cores
+        if cores > 1:
+            allc = cpu_oracle_sample(args.config, args.cpu_seconds, threads=cores, R=256)
+            cpu["all_cores"] = {k: allc[k] for k in ("value", "cores", "sample")}
+    batched = served = None
+    if world == 1 and not args.no_batch_serve:
+        b = batch_measure(args)
+        batched = {k: b[k] for k in ("ratio", "ratio_vs_default_plain", "value", "plain_value", "batch_s", "plain_s",
+                                     "graph_build_and_setup_ms", "bit_identical_to_plain", "instances")}
+        sv = serve_measure(args)
+        served = {k: sv[k] for k in ("ratio", "value", "plain_value", "p50_ms", "p99_ms", "plain_p50_ms",
+                                     "plain_p99_ms", "requests", "bit_identical_to_plain")}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int8/bit spins, int32 energies, fp64 weights",
@@ -354,28 +467,29 @@ def run_ours(args, rank, world, dist):
             "accept_rate": acc_rate,
             "best_cut": int(cut), "best_step": int(best_step), "time_to_best_ms": t_best,
             "e2e": e2e, "gpu_launches": stats_acc["kernel_launches"],
-            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "peaks": peaks_src}
+            "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "peaks": peaks_src,
+            "batched": batched, "served": served}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # -------------------------------------------------------------- batched ---
-def run_batch(args):
+def batch_measure(args, reps: int = 2):
     """64 mixed instances (N ~ U[800, 20000]; random p = 12/(N-1), signed torus,
     Delaunay; R cycling 1024/4096/16384), beta 0.1 -> 3.0 in 200 steps, 4 sweeps:
     each instance annealed alone in turn (plain) vs all in one batched launch
-    captured in a CUDA graph; kernel shapes from the autotuner."""
+    captured in a CUDA graph; kernel shapes from the autotuner. Both arms are
+    timed the same way: host wall-clock from the first population set-up to
+    the last result read back (graph capture and instantiation included in the
+    batched arm, and also reported on their own)."""
     import tempfile
 
     import torch
 
     from paper_2510_21105_gb300 import autotune
     from paper_2510_21105_gb300 import binding as B
-    from paper_2510_21105_gb300 import build as build_mod
     from paper_2510_21105_gb300 import workloads as wl
 
-    build_mod.build()
-    torch.cuda.set_device(0)
     K, S = 200, 4
     betas = wl.linear_betas(0.1, 3.0, K)
     inst = wl.batch_instances(args.instances, seed=0)
@@ -383,7 +497,7 @@ def run_batch(args):
     t0 = time.perf_counter()
     opts, opts_b = [], []
     cand = [c for c in autotune.CANDIDATES if c.get("variant") in (1, 3) or c.get("field_bits") == 7]
-    for i, it in enumerate(inst):
+    for it in inst:
         g = it["graph"]
         o, _ = autotune.tune(g, betas, it["R"], S, seed=it["seed"], steps=1, cache_path=cache, candidates=cand)
         ob, _ = autotune.tune(g, betas, it["R"], S, seed=it["seed"], steps=1, cache_path=cache,
@@ -393,44 +507,59 @@ def run_batch(args):
     tune_s = time.perf_counter() - t0
     attempts = sum(it["graph"].n * it["R"] * S * K for it in inst)
     anns = [B.Annealer.from_graph(it["graph"]) for it in inst]
-    # plain: one instance after another, each its own pa_anneal
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ann0 = anns[0]
-    ann0.anneal(betas, inst[0]["R"], S, inst[0]["seed"], **opts[0])   # warm-up
-    torch.cuda.synchronize()
-    ev0.record()
-    plain_best = []
-    for ann, it, o in zip(anns, inst, opts):
-        ann.anneal(betas, it["R"], S, it["seed"], **o)
-        plain_best.append(ann.best_record())
-    ev1.record()
-    torch.cuda.synchronize()
-    plain_ms = ev0.elapsed_time(ev1)
-    # plain with the library's default layout choice (no per-instance tuning)
-    ev0.record()
-    for ann, it in zip(anns, inst):
-        ann.anneal(betas, it["R"], S, it["seed"])
-    ev1.record()
-    torch.cuda.synchronize()
-    plain_default_ms = ev0.elapsed_time(ev1)
+
+    def plain(option_list):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        best = []
+        for ann, it, o in zip(anns, inst, option_list):
+            ann.anneal(betas, it["R"], S, it["seed"], **o)
+            best.append(ann.best_record())
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, best
+
+    anns[0].anneal(betas, inst[0]["R"], S, inst[0]["seed"], **opts[0])   # warm-up
+    plain_s, plain_best = plain(opts)
+    plain_default_s, _ = plain([{} for _ in inst])
     items = [(ann, betas, it["R"], S, it["seed"], K, o) for ann, it, o in zip(anns, inst, opts_b)]
-    B.pa_batch_anneal(items, n_streams=args.streams, use_graph=True)   # warm-up (and graph build)
-    times = [B.pa_batch_anneal(items, n_streams=args.streams, use_graph=True) for _ in range(max(args.steps, 1))]
-    batch_ms = statistics.median(times)
-    same = all(ann.best_record() == b for ann, b in zip(anns, plain_best))
+
+    def batched():
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        dev_ms = B.pa_batch_anneal(items, n_streams=args.streams, use_graph=bool(args.use_graph))
+        best = [ann.best_record() for ann in anns]
+        torch.cuda.synchronize()
+        return time.perf_counter() - t, dev_ms, best
+
+    batched()   # warm-up
+    runs = [batched() for _ in range(max(reps, 1))]
+    batch_s = statistics.median(r[0] for r in runs)
+    dev_ms = statistics.median(r[1] for r in runs)
+    same = all(b == p for b, p in zip(runs[-1][2], plain_best))
     for a in anns:
         a.close()
-    line = {"mode": "batch", "metric": "batched attempts/s (64 mixed instances) vs plain one-instance-per-launch",
-            "value": attempts / (batch_ms / 1e3), "unit": UNIT, "plain_value": attempts / (plain_ms / 1e3),
-            "ratio": plain_ms / batch_ms, "batch_ms": batch_ms, "plain_ms": plain_ms,
-            "plain_default_value": attempts / (plain_default_ms / 1e3), "plain_default_ms": plain_default_ms,
-            "ratio_vs_default_plain": plain_default_ms / batch_ms,
-            "bit_identical_to_plain": same, "instances": len(inst), "attempts": attempts,
-            "autotune_s": tune_s,
+    return {"value": attempts / batch_s, "plain_value": attempts / plain_s, "ratio": plain_s / batch_s,
+            "plain_default_value": attempts / plain_default_s, "ratio_vs_default_plain": plain_default_s / batch_s,
+            "batch_s": batch_s, "plain_s": plain_s, "plain_default_s": plain_default_s,
+            "batch_device_ms": dev_ms, "graph_build_and_setup_ms": batch_s * 1e3 - dev_ms,
+            "bit_identical_to_plain": same, "instances": len(inst), "attempts": attempts, "autotune_s": tune_s,
             "layouts_plain": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts)),
-            "layouts_batched": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts_b)),
+            "layouts_batched": dict(collections.Counter(json.dumps(o, sort_keys=True) for o in opts_b))}
+
+
+def run_batch(args):
+    from paper_2510_21105_gb300 import build as build_mod
+    import torch
+
+    build_mod.build()
+    torch.cuda.set_device(0)
+    r = batch_measure(args, reps=args.steps)
+    line = {"mode": "batch", "metric": "batched attempts/s (64 mixed instances) vs plain one-instance-per-launch",
+            "unit": UNIT, **r,
             "config": {"workload": "N~U[800,20000] random(p=12/(N-1))/torus/Delaunay, R 1024/4096/16384, "
-                                   "beta 0.1->3.0 K=200 S=4", "use_graph": True, "n_streams": args.streams}}
+                                   "beta 0.1->3.0 K=200 S=4", "n_streams": args.streams,
+                       "timing": "host wall-clock, first set-up to last result, both arms"}}
+    line["config"]["use_graph"] = bool(args.use_graph)
     print(json.dumps(line), flush=True)
     return 0
 
@@ -458,13 +587,13 @@ def _serve_trace(seconds, rate, seed=1):
     return trace
 
 
-def _serve(trace, betas, slots, saturated):
+def _serve(trace, betas, slots, saturated, steps_per_tick=8):
     """saturated: other requests keep the GPU full, so each request uses the
     kernel with the cheapest attempt (multi-spin coded); otherwise each uses
     the automatic choice for a GPU of its own."""
     from paper_2510_21105_gb300 import binding as B
 
-    with B.Server(200 << 30, n_streams=slots, steps_per_tick=8) as srv:
+    with B.Server(200 << 30, n_streams=slots, steps_per_tick=steps_per_tick) as srv:
         ids = []
         t0 = time.perf_counter()
         for at, g, R, seed in trace:
@@ -488,27 +617,35 @@ def _serve(trace, betas, slots, saturated):
                 best=[(r["energy"], r["step"], r["sweep"], r["slot"]) for r in out])
 
 
+def serve_measure(args):
+    """Served trace with continuous batching (16 slots) against the same trace
+    served one request at a time."""
+    from paper_2510_21105_gb300 import workloads as wl
+
+    betas = wl.linear_betas(0.1, 3.0, 200)
+    trace = _serve_trace(args.serve_seconds, args.rate)
+    served = _serve(trace, betas, slots=args.slots, saturated=True, steps_per_tick=args.tick)
+    plain = _serve(trace, betas, slots=1, saturated=False)
+    return {"value": served["attempts_per_s"], "plain_value": plain["attempts_per_s"],
+            "ratio": served["attempts_per_s"] / plain["attempts_per_s"],
+            "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"],
+            "plain_p50_ms": plain["p50_ms"], "plain_p99_ms": plain["p99_ms"],
+            "requests": len(trace), "bit_identical_to_plain": served["best"] == plain["best"]}
+
+
 def run_serve(args):
     import torch
 
     from paper_2510_21105_gb300 import build as build_mod
-    from paper_2510_21105_gb300 import workloads as wl
 
     build_mod.build()
     torch.cuda.set_device(0)
-    betas = wl.linear_betas(0.1, 3.0, 200)
-    trace = _serve_trace(args.serve_seconds, args.rate)
-    served = _serve(trace, betas, slots=16, saturated=True)
-    plain = _serve(trace, betas, slots=1, saturated=False)
+    r = serve_measure(args)
     line = {"mode": "serve", "metric": "served attempts/s with continuous batching vs plain one-at-a-time",
-            "value": served["attempts_per_s"], "unit": UNIT, "plain_value": plain["attempts_per_s"],
-            "ratio": served["attempts_per_s"] / plain["attempts_per_s"],
-            "p50_ms": served["p50_ms"], "p99_ms": served["p99_ms"],
-            "plain_p50_ms": plain["p50_ms"], "plain_p99_ms": plain["p99_ms"],
-            "requests": len(trace), "bit_identical_to_plain": served["best"] == plain["best"],
+            "unit": UNIT, **r,
             "config": {"workload": f"Poisson {args.rate}/s over {args.serve_seconds} s; random/torus N~U[800,20000]; "
-                                   "R=round(2^U[10,15]); beta 0.1->3.0 K=200 S=4", "slots": 16,
-                       "hbm_budget_gb": 200, "steps_per_tick": 8}}
+                                   "R=round(2^U[10,15]); beta 0.1->3.0 K=200 S=4", "slots": args.slots,
+                       "hbm_budget_gb": 200, "steps_per_tick": args.tick}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -519,6 +656,8 @@ def main():
         return run_batch(args)
     if args.mode == "serve":
         return run_serve(args)
+    if args.mode == "oracle":
+        return run_oracle_plan(args)
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

@@ -446,7 +446,8 @@ int pa_resample_noalloc(const int32_t *energies, int32_t R, double beta_prev, do
  *                        counts; rows arrive in new-slot order.
  * Device pointers: energies int32[n], scratch of pa_shard_scratch_bytes(n)
  * bytes (caller-owned, kept between pa_shard_partials and pa_shard_parents),
- * src int32[new_hi - new_lo], counts int32[n] or NULL. stream: cudaStream_t or
+ * src int32[new_hi - new_lo] (may be empty: a rank whose parents fill no new
+ * slot gathers nothing), counts int32[n] or NULL. stream: cudaStream_t or
  * NULL. pa_shard_plan and pa_resample_offset are host-only and need no GPU.
  * Errors: PA_EINVAL (sizes, layout, schedule), PA_ECUDA.
  */

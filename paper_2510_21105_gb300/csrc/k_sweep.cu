@@ -572,8 +572,10 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
 // 15 of a lane is "reject or tie" and bit 15 of lane - 1 is "reject". A byte
 // permute replicating those sign bits turns the four lanes of a group into
 // byte masks. A tie (probability 1/256 per uncertain attempt) is settled by
-// the low 24 bits of the uniform, drawn only then. Accepted replicas flip
-// with one XOR.
+// the low 24 bits of the uniform, drawn only then: the ties of a warp's items
+// are queued and settled by all 32 lanes together before the class barrier
+// (one tail Philox call per lane instead of one per tying lane while the
+// others wait). Accepted replicas flip with one XOR.
 // Byte permute with sign replication: each selector nibble with bit 3 set
 // fills its result byte with the top bit of the selected byte.
 __device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t b, uint32_t sel) {
@@ -763,7 +765,7 @@ __device__ __forceinline__ uint32_t msc_entry(int i, bool pk, const uint32_t *ta
 template <int NPL, bool WEIGHTED>
 __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t *Wsm, const uint32_t *T256, int p,
                                              uint32_t x, uint32_t c3, int blk, int32_t *Eacc,
-                                             uint32_t (&ebias)[8]) {
+                                             uint32_t (&ebias)[8], uint32_t &tent) {
     const uint32_t vid = __ldg(&a.g.vid[p]);
     uint32_t pl[NPL];
 #pragma unroll
@@ -870,8 +872,11 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
         }
     }
     uint32_t tie = acct32 & ~acc32;
-    if (tie) {   // rare: the low 24 bits of the uniform decide
+    tent = 0u;
+    if (tie) {   // the low 24 bits of the uniform decide: the item's first tie is queued for
+                 // the warp (msc_queue_tie), further ties of the same item are settled here
         const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
+        bool first = true;
         do {
             const int bit = __ffs(tie) - 1;
             tie &= tie - 1u;
@@ -881,6 +886,11 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
             for (int j = 1; j < 8; ++j)
                 if (g == j) rg = r[j];
             const int m = 2 * (int)((rg >> (bit & 24)) & 0xFFu) - (int)deg;
+            if (first) {   // the item's first tie goes to the warp's queue
+                tent = 0x80000000u | (uint32_t)p << 13 | (uint32_t)bit << 8 | (uint32_t)m;
+                first = false;
+                continue;
+            }
             const uint32_t T = __ldg(&tab[m]);
             const int rep = 4 * (bit & 7) + (bit >> 3);
             if (sweep_tail_bits(vid, 32u * blk + rep, (uint32_t)a.k, c3, a.key0, a.key1) < (T & 0xFFFFFFu)) {
@@ -890,6 +900,50 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
         } while (tie);
     }
     return acc32;
+}
+
+// Ties queued by the items of a warp (entry = flag | p << 13 | bit << 8 | m)
+// are settled together: each lane takes one entry, draws the low 24 bits of
+// its uniform and applies an accepted flip to the word (and its copy in the
+// peer CTA), the energy and the accept count. Items of one colour class never
+// read each other's words, so a flip applied after the other items of the
+// class is the same as one applied at once; every queue is emptied before the
+// class barrier.
+__device__ __forceinline__ void msc_drain_ties(const SweepArgs &a, const uint32_t *TQ, int qc, uint32_t *Wsm,
+                                               uint32_t *Wpeer, int32_t *Eacc, int blk, uint32_t c3, uint32_t vmask,
+                                               uint32_t &nacc, int lane) {
+    __syncwarp();
+    const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
+    for (int i = lane; i < qc; i += 32) {
+        const uint32_t e = TQ[i];
+        const int p = (int)((e >> 13) & 0xFFFFu), bit = (int)((e >> 8) & 31u), m = (int)(e & 0xFFu);
+        const int rep = 4 * (bit & 7) + (bit >> 3);
+        const uint32_t T = __ldg(&tab[m]);
+        if (sweep_tail_bits(__ldg(&a.g.vid[p]), 32u * blk + rep, (uint32_t)a.k, c3, a.key0, a.key1) <
+            (T & 0xFFFFFFu)) {
+            atomicXor(&Wsm[p], 1u << bit);
+            if (Wpeer) atomicXor(&Wpeer[p], 1u << bit);
+            atomicAdd(&Eacc[rep], 2 * m);
+            nacc += (vmask >> bit) & 1u;
+        }
+    }
+    __syncwarp();
+}
+
+// Appends the lanes' queue entries (tent != 0) to the warp's tie queue; drains
+// it once it holds more than 32 entries (capacity 64).
+__device__ __forceinline__ void msc_queue_tie(const SweepArgs &a, uint32_t *TQ, int &qc, uint32_t tent, uint32_t *Wsm,
+                                              uint32_t *Wpeer, int32_t *Eacc, int blk, uint32_t c3, uint32_t vmask,
+                                              uint32_t &nacc, int lane) {
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, tent != 0u);
+    if (bal) {
+        if (tent) TQ[qc + __popc(bal & ((1u << lane) - 1u))] = tent;
+        qc += __popc(bal);
+        if (qc > 32) {
+            msc_drain_ties(a, TQ, qc, Wsm, Wpeer, Eacc, blk, c3, vmask, nacc, lane);
+            qc = 0;
+        }
+    }
 }
 
 template <int NPL, bool WEIGHTED, int NTB, int MINB>
@@ -905,6 +959,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     int32_t *Eacc = cls + csz;      // [32]
     int32_t *PS = Eacc + 32;        // [32]
     int32_t *misc = PS + 32;        // best E, step, sweep, slot, copy-from (r+1), changed
+    uint32_t *TQ = reinterpret_cast<uint32_t *>(misc + 8) + (threadIdx.x >> 5) * 64;   // [warps][64] tie queues
 
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
@@ -940,20 +995,25 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
             for (int c = 0; c < a.g.ncol; ++c) {
                 const int p0 = cls[c], p1 = cls[c + 1];
                 const int nr = (p1 - p0 + NT - 1) / NT;   // rounds of the class, uniform over the CTA
+                int qc = 0;   // entries in this warp's tie queue
                 for (int rd = 0; rd < nr; ++rd) {
                     const int p = p0 + tid + rd * NT;
+                    uint32_t tent = 0u;
                     if (p < p1) {
                         const uint32_t x = Wsm[p];
-                        const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, Eacc, ebias);
+                        const uint32_t acc32 =
+                            msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, Eacc, ebias, tent);
                         if (acc32) {
                             Wsm[p] = x ^ acc32;
                             nacc += __popc(acc32 & vmask);
                         }
                         ++cnt;
                     }
+                    msc_queue_tie(a, TQ, qc, tent, Wsm, nullptr, Eacc, blk, c3, vmask, nacc, lane);
                     if (MscPackedE<NPL>::value && ((rd & 3) == 3 || rd == nr - 1))
                         msc_flush_energy(ebias, cnt, Eacc, lane);
                 }
+                if (qc) msc_drain_ties(a, TQ, qc, Wsm, nullptr, Eacc, blk, c3, vmask, nacc, lane);
                 __syncthreads();
             }
             if (tid == 0) {
@@ -1025,6 +1085,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
     int32_t *misc = PS + 32;        // best E, step, sweep, slot, copy-from (r+1), changed
     uint32_t *Wpeer = cluster.map_shared_rank(Wsm, rank ^ 1);
     int32_t *E0 = cluster.map_shared_rank(Eacc, 0);
+    uint32_t *TQ = reinterpret_cast<uint32_t *>(misc + 8) + (threadIdx.x >> 5) * 64;   // [warps][64] tie queues
 
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
@@ -1060,11 +1121,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
             for (int c = 0; c < a.g.ncol; ++c) {
                 const int p0 = cls[c], p1 = cls[c + 1];
                 const int nr = (p1 - p0 + 2 * NT - 1) / (2 * NT);   // rounds, uniform over the cluster
+                int qc = 0;   // entries in this warp's tie queue
                 for (int rd = 0; rd < nr; ++rd) {
                     const int p = p0 + 2 * tid + rank + rd * 2 * NT;
+                    uint32_t tent = 0u;
                     if (p < p1) {
                         const uint32_t x = Wsm[p];
-                        const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, E0, ebias);
+                        const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, E0, ebias, tent);
                         if (acc32) {
                             Wsm[p] = x ^ acc32;
                             Wpeer[p] = x ^ acc32;
@@ -1072,9 +1135,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
                         }
                         ++cnt;
                     }
+                    msc_queue_tie(a, TQ, qc, tent, Wsm, Wpeer, E0, blk, c3, vmask, nacc, lane);
                     if (MscPackedE<NPL>::value && ((rd & 3) == 3 || rd == nr - 1))
                         msc_flush_energy(ebias, cnt, E0, lane);
                 }
+                if (qc) msc_drain_ties(a, TQ, qc, Wsm, Wpeer, E0, blk, c3, vmask, nacc, lane);
                 cluster.sync();
             }
             if (rank == 0 && tid == 0) {
@@ -1173,7 +1238,8 @@ void *select_kernel(int G, int fb, bool weighted, int threads, int mmax) {
 
 size_t sweep_smem_bytes(const GraphDev &g, int G, int field_bits, int threads) {
     if (field_bits == 1 || field_bits == 2)   // multi-spin coded: 32 replicas per word (2: CTA pairs)
-        return (size_t)g.np * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + (32 + 32 + 8) * 4;
+        return (size_t)g.np * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + (32 + 32 + 8) * 4 +
+               (size_t)(threads / 32) * 64 * 4;   // tie queues
     if (field_bits == 7)
         return (size_t)(g.np + 32) * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + 16 * 4 +
                (size_t)((((g.np + 31) / 32) + 1) & ~1) * 4 + (size_t)(threads / 32) * PK_QCAP * 8;

@@ -59,12 +59,18 @@ __global__ void __launch_bounds__(PROBE_THREADS) k_probe_smem(int iters, uint32_
     __shared__ __align__(16) uint32_t buf[SMEM_WORDS];
     for (int i = threadIdx.x; i < SMEM_WORDS; i += blockDim.x) buf[i] = (uint32_t)i * 2654435761u;
     __syncthreads();
-    const uint4 *v = reinterpret_cast<const uint4 *>(buf);
+    // Lanes read consecutive 16-byte words (no bank conflicts). The loads are
+    // volatile so that the compiler keeps every one of them: the addresses
+    // repeat every four iterations and nothing writes the buffer in the loop.
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(buf);
     uint32_t acc = 0;
-    int idx = threadIdx.x;   // lanes read consecutive 16-byte words: no bank conflicts
+    int idx = threadIdx.x;
     for (int i = 0; i < iters; ++i) {
-        const uint4 w = v[idx];
-        acc ^= w.x ^ w.y ^ w.z ^ w.w;
+        uint32_t w0, w1, w2, w3;
+        asm volatile("ld.volatile.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(w0), "=r"(w1), "=r"(w2), "=r"(w3)
+                     : "r"(base + 16u * (uint32_t)idx));
+        acc ^= w0 ^ w1 ^ w2 ^ w3;
         idx = (idx + PROBE_THREADS) & (SMEM_WORDS / 4 - 1);
     }
     if (sink && acc == 0x12345678u) sink[0] = acc;

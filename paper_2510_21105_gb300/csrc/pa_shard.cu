@@ -257,7 +257,7 @@ int pa_shard_plan(int32_t G, int32_t g, int32_t R, const double *A_all, const ui
 
 int pa_shard_parents(const void *scratch, int32_t n, int32_t R, uint32_t o, const pa_shard_step *step,
                      int32_t *src, int32_t *counts, void *stream) {
-    if (!scratch || !step || !src || n < 1 || n > PA_SHARD_MAX_SLOTS || R < 1 || R > 65536) return PA_EINVAL;
+    if (!scratch || !step || (!src && step->new_hi > step->new_lo) || n < 1 || n > PA_SHARD_MAX_SLOTS || R < 1 || R > 65536) return PA_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const ShardScratch s = scratch_view(const_cast<void *>(scratch), n);
     k_shard_parents<<<(n + 255) / 256, 256, 0, st>>>(s, n, step->P_base, step->T, R, o, step->new_lo, src, counts);
@@ -266,8 +266,8 @@ int pa_shard_parents(const void *scratch, int32_t n, int32_t R, uint32_t o, cons
 
 int pa_shard_gather(const int8_t *spins, const int32_t *energies, int32_t ncols, const int32_t *src, int32_t nout,
                     int8_t *spins_out, int32_t *energies_out, void *stream) {
+    if (nout == 0) return PA_OK;   // a rank whose parents fill no new slot sends nothing
     if (!spins || !src || !spins_out || ncols < 1 || nout < 0 || (energies && !energies_out)) return PA_EINVAL;
-    if (nout == 0) return PA_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int grid = nout < 4096 ? nout : 4096;
     k_shard_gather<<<grid, 128, 0, st>>>(spins, energies, ncols, src, nout, spins_out, energies_out);

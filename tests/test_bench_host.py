@@ -7,34 +7,50 @@ import bench
 
 def test_smem_bytes_per_attempt_by_layout():
     d = 2 * 41459 / 7000   # mean degree of the G63-shaped graph
-    # multi-spin coded: neighbour words + own word read and written per
-    # 32-replica item, plus two 4-byte table halves per attempt
-    assert bench.smem_bytes_per_attempt(("k_sweep_msc+pair", 256), d, 0.06) == pytest.approx((4 * d + 8) / 32 + 8)
-    assert bench.smem_bytes_per_attempt(("k_sweep_msc_pair", 256), 4.0, 0.5) == pytest.approx(0.75 + 8)
+    # multi-spin coded: the measurement plan's (8 + 6 d) / 32 -- own word read
+    # and written, a 4-byte neighbour word and its 2-byte index per bond
+    assert bench.smem_bytes_per_attempt(("k_sweep_msc+pair", 256), d, 0.06) == pytest.approx((8 + 6 * d) / 32)
+    assert bench.smem_bytes_per_attempt(("k_sweep_msc_pair", 256), 4.0, 0.5) == pytest.approx(1.0)
     # 4-replica layouts: byte read + written, threshold word, and neighbour
     # field bytes read + written on an accepted flip
     assert bench.smem_bytes_per_attempt(("k_sweep_packed", 128), 10.0, 0.1) == pytest.approx(6 + 2.0)
 
 
+def test_msc_ops_per_attempt_counts_each_part():
+    # per 32-replica item: 4.5 ops per bond, 48 for the count bytes, 80 for two
+    # Philox calls, 16 per 4-replica group for the decision and 4 for energies
+    assert bench.msc_ops_per_attempt(0.0) == pytest.approx((48 + 80 + 128 + 32) / 32)
+    assert bench.msc_ops_per_attempt(12.0) - bench.msc_ops_per_attempt(4.0) == pytest.approx(4.5 * 8 / 32)
+
+
 def test_sweep_roofline_fractions():
     stats = {"sweep_ms": 1500.0, "sweep_launches": 1000}
     attempts = 7000 * 16384 * 10
-    r = bench.sweep_roofline(stats, attempts, {"sm_max_mhz": 2000.0}, ("k_sweep_msc+pair", 256), 12.0, 0.06)
+    probe = {"int_ops_per_s": 30e12, "philox_words_per_s": 1.6e12, "smem_bytes_per_s": 38e12, "sms": 152}
+    r = bench.sweep_roofline(stats, attempts, probe, 2000.0, ("k_sweep_msc+pair", 256), 12.0, 0.06)
     t = 1.5e-3
+    aps = attempts / t
     assert r["bound"] == "alu" and r["unit"] == "Tops/s"
     assert r["avg_launch_ms"] == pytest.approx(1.5)
-    assert r["achieved"] == pytest.approx(attempts * bench.OPS_PER_ATTEMPT / t / 1e12)
-    assert r["peak"] == pytest.approx(bench.SMS * 128 * 2000e6 / 1e12)
-    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["attempts_per_s_in_kernel"] == pytest.approx(attempts / t)
-    smem = attempts * r["smem_bytes_per_attempt"] / t
-    assert r["smem_frac"] == pytest.approx(smem / (bench.SMS * 128 * 2000e6))
-    assert r["traffic"] == bench.SWEEP_TRAFFIC.get(("k_sweep_msc+pair", 256))
-    packed = bench.sweep_roofline(stats, attempts, {}, ("k_sweep_packed", 128), 12.0, 0.06)
-    assert packed["traffic"] == bench.SWEEP_TRAFFIC[("k_sweep_packed", 128)]
-    # a kernel with no ncu capture reports no traffic; no launches, no line
-    assert bench.sweep_roofline(stats, attempts, {}, ("k_sweep", 512), 12.0, 0.06)["traffic"] is None
-    assert bench.sweep_roofline({"sweep_ms": 0.0, "sweep_launches": 0}, attempts, {}, ("k_sweep", 512), 12.0, 0.06) is None
+    assert r["attempts_per_s_in_kernel"] == pytest.approx(aps)
+    assert r["achieved"] == pytest.approx(aps * bench.msc_ops_per_attempt(12.0) / 1e12)
+    assert r["peak"] == pytest.approx(30.0) and r["frac"] == pytest.approx(r["achieved"] / 30.0)
+    assert r["peak_derived"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
+    assert r["smem_frac"] == pytest.approx(aps * (8 + 6 * 12.0) / 32 / 38e12)
+    assert r["smem_frac_vs_derived"] == pytest.approx(aps * (8 + 6 * 12.0) / 32 / (152 * 128 * 2000e6))
+    assert r["smem_target_met"] is False
+    assert r["philox_frac"] == pytest.approx(aps * 0.25 / 1.6e12)
+    # without a probe the unit-count peak is used
+    r2 = bench.sweep_roofline(stats, attempts, None, 2000.0, ("k_sweep_msc+pair", 256), 12.0, 0.06)
+    assert r2["peak"] == pytest.approx(r2["peak_derived"]) and r2["philox_frac"] is None
+    # traffic only while the captured source is the one that runs
+    bench.SWEEP_TRAFFIC["k_sweep_msc+pair"] = (123.0e6, bench.sweep_source_sha())
+    assert bench.sweep_roofline(stats, attempts, probe, 2000.0, ("k_sweep_msc+pair", 256), 12.0, 0.06)["traffic"] == 123.0e6
+    bench.SWEEP_TRAFFIC["k_sweep_msc+pair"] = (123.0e6, "0000000000000000")
+    assert bench.sweep_roofline(stats, attempts, probe, 2000.0, ("k_sweep_msc+pair", 256), 12.0, 0.06)["traffic"] is None
+    del bench.SWEEP_TRAFFIC["k_sweep_msc+pair"]
+    assert bench.sweep_roofline({"sweep_ms": 0.0, "sweep_launches": 0}, attempts, probe, 2000.0, ("k_sweep", 512),
+                                12.0, 0.06) is None
 
 
 def test_clock_summary_reads_samples_and_reasons(tmp_path):
