@@ -229,7 +229,7 @@ def run_reference(args, rank, world):
 # tail launches of the multi-spin-coded sweep, or the one launch of another
 # layout), from one ncu capture, with the SHA-256 prefix of the sweep source it
 # was taken on: reported only while that source is the one that runs.
-SWEEP_TRAFFIC = {}
+SWEEP_TRAFFIC = {"k_sweep_msc+pair": ((103.112448 + 44.893440 + 12.872960) * 1e6, "1435957358578f15")}
 SWEEP_SRC = os.path.join(ROOT, "paper_2510_21105_gb300", "csrc", "k_sweep.cu")
 INT_LANES_PER_SM = 128   # ALU pipe 64 + FMA pipe 64 integer lanes per SM and clock (unit counts)
 SMEM_BYTES_PER_SM = 128  # shared-memory bytes per SM and clock (32 banks x 4 B)

@@ -145,7 +145,7 @@ def _anneal(argv):
     out = dict(config=name, n=g.n, m=g.m, R=c["R"], S=c["S"], steps=K, seed=c["seed"], best_cut=cut,
                best_step=step, best_sweep=sweep, wall_s=dt, attempts=st["attempts"],
                nlm_moves=int(ss_nlm[0]), nlm_flips=int(ss_nlm[1]),
-               accepts=st["accepts"], device_ms=st["anneal_ms"],
+               accepts=st["accepts"], device_ms=st["anneal_ms"], time_to_best_ms=st["t_best_ms"],
                attempts_per_s=st["attempts"] / max(st["anneal_ms"], 1e-9) * 1e3)
     if a.hex or a.save_hex:
         h = hexconfig.encode(cfg)

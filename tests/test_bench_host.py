@@ -44,13 +44,26 @@ def test_sweep_roofline_fractions():
     r2 = bench.sweep_roofline(stats, attempts, None, 2000.0, ("k_sweep_msc+pair", 256), 12.0, 0.06)
     assert r2["peak"] == pytest.approx(r2["peak_derived"]) and r2["philox_frac"] is None
     # traffic only while the captured source is the one that runs
-    bench.SWEEP_TRAFFIC["k_sweep_msc+pair"] = (123.0e6, bench.sweep_source_sha())
-    assert bench.sweep_roofline(stats, attempts, probe, 2000.0, ("k_sweep_msc+pair", 256), 12.0, 0.06)["traffic"] == 123.0e6
-    bench.SWEEP_TRAFFIC["k_sweep_msc+pair"] = (123.0e6, "0000000000000000")
-    assert bench.sweep_roofline(stats, attempts, probe, 2000.0, ("k_sweep_msc+pair", 256), 12.0, 0.06)["traffic"] is None
-    del bench.SWEEP_TRAFFIC["k_sweep_msc+pair"]
+    saved = dict(bench.SWEEP_TRAFFIC)
+    try:
+        bench.SWEEP_TRAFFIC["k_sweep_msc+pair"] = (123.0e6, bench.sweep_source_sha())
+        r3 = bench.sweep_roofline(stats, attempts, probe, 2000.0, ("k_sweep_msc+pair", 256), 12.0, 0.06)
+        assert r3["traffic"] == 123.0e6
+        bench.SWEEP_TRAFFIC["k_sweep_msc+pair"] = (123.0e6, "0000000000000000")
+        r4 = bench.sweep_roofline(stats, attempts, probe, 2000.0, ("k_sweep_msc+pair", 256), 12.0, 0.06)
+        assert r4["traffic"] is None
+    finally:
+        bench.SWEEP_TRAFFIC.clear()
+        bench.SWEEP_TRAFFIC.update(saved)
     assert bench.sweep_roofline({"sweep_ms": 0.0, "sweep_launches": 0}, attempts, probe, 2000.0, ("k_sweep", 512),
                                 12.0, 0.06) is None
+
+
+def test_recorded_traffic_belongs_to_the_current_sweep_source():
+    """The DRAM traffic the bench line reports was captured on the sweep source
+    that is checked in (else it reports none)."""
+    entry = bench.SWEEP_TRAFFIC.get("k_sweep_msc+pair")
+    assert entry is None or entry[1] == bench.sweep_source_sha()
 
 
 def test_clock_summary_reads_samples_and_reasons(tmp_path):
