@@ -171,15 +171,17 @@ def host_cores() -> int:
 
 def run_oracle_plan(args):
     """The oracle timing plan of the measurement: the small random-graph
-    workload (N=800, R=256, K=100, S=4) in full, and the G63-shaped graph with
-    R=256 over all K=1000 steps, on one host core and on all of them (the
-    single-thread run of the latter is bounded to --oracle-steps steps)."""
+    workload (N=800, R=256, K=100, S=4) in full, and the G63-shaped graph and
+    the 100 x 100 torus with R=256 over all their steps, on one host core and on
+    all of them (the single-thread runs of the latter two are bounded to
+    --oracle-steps steps)."""
     import oracle
     from paper_2510_21105_gb300 import workloads as wl
 
     cores = host_cores()
     out = {"mode": "oracle", "unit": UNIT, "nproc": cores, "runs": []}
-    for name, R, K1 in (("gnp800", 256, None), ("g63like", 256, args.oracle_steps)):
+    for name, R, K1 in (("gnp800", 256, None), ("g63like", 256, args.oracle_steps),
+                        ("torus100", 256, args.oracle_steps)):
         c = wl.CONFIGS[name]
         g = c["graph"]()
         betas = wl.linear_betas(*c["beta"], c["K"])
@@ -229,7 +231,7 @@ def run_reference(args, rank, world):
 # tail launches of the multi-spin-coded sweep, or the one launch of another
 # layout), from one ncu capture, with the SHA-256 prefix of the sweep source it
 # was taken on: reported only while that source is the one that runs.
-SWEEP_TRAFFIC = {"k_sweep_msc+pair": ((103.112448 + 44.893440 + 12.872960) * 1e6, "1435957358578f15")}
+SWEEP_TRAFFIC = {"k_sweep_msc+pair": ((102.873600 + 41.293056 + 12.874496) * 1e6, "4f5d6dab7dc7f9b5")}
 SWEEP_SRC = os.path.join(ROOT, "paper_2510_21105_gb300", "csrc", "k_sweep.cu")
 INT_LANES_PER_SM = 128   # ALU pipe 64 + FMA pipe 64 integer lanes per SM and clock (unit counts)
 SMEM_BYTES_PER_SM = 128  # shared-memory bytes per SM and clock (32 banks x 4 B)

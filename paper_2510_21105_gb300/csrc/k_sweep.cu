@@ -40,6 +40,29 @@ __device__ __forceinline__ void transpose4x4_bytes(uint32_t w0, uint32_t w1, uin
     o[3] = __byte_perm(a_hi, b_hi, 0x7632);
 }
 
+// Byte permute with sign replication: each selector nibble with bit 3 set
+// fills its result byte with the top bit of the selected byte.
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// Entry i of a decision table in 16-bit lanes (the multi-spin-coded and the
+// packed kernels): E(m) in both halves, m = i - 32 for counts of |m| <= 31
+// kept as byte offsets 4m + 128, else m = i - 128 (word index). With the top
+// byte of the uniform, lane = 128 top + E is below 0x8000 iff the move is
+// accepted, 0x8000 exactly on a tie that the low bits decide.
+__device__ __forceinline__ uint32_t msc_entry(int i, bool pk, const uint32_t *tab, int mmax) {
+    const int m = pk ? i - 32 : i - 128;
+    uint32_t e = 1u;   // m <= 0: always accepted
+    if (m > 0) {
+        const uint32_t T = m <= mmax ? tab[m] : 0u;
+        e = T == 0u ? 0x8040u : 0x8000u - 128u * (T >> 24) + ((T & 0xFFFFFFu) == 0u ? 64u : 0u);
+    }
+    return e * 0x00010001u;
+}
+
 template <int G, int FB, bool WEIGHTED>
 __device__ __forceinline__ void sweep_item(uint32_t *__restrict__ Ssm, uint32_t *__restrict__ Hsm,
                                            const uint32_t *__restrict__ Tt, const SweepArgs &a,
@@ -300,6 +323,20 @@ struct PkItem {
     uint32_t b, mb, smask, acc;
 };
 
+// Ties of the top byte in a packed item (rare): the low 24 bits of the
+// uniform decide.
+__device__ __forceinline__ uint32_t pk_settle_ties(const SweepArgs &a, uint32_t acc, uint32_t tie, uint32_t mb,
+                                                uint32_t vid, uint32_t c1, uint32_t c3) {
+    const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
+    do {
+        const int q = __ffs(tie) - 1;
+        tie &= tie - 1u;
+        const uint32_t T = __ldg(&tab[(int)((mb >> (8 * q)) & 0xFFu) - 128]);
+        if (sweep_tail_bits(vid, 4u * c1 + q, (uint32_t)a.k, c3, a.key0, a.key1) < (T & 0xFFFFFFu)) acc |= 1u << q;
+    } while (tie);
+    return acc;
+}
+
 __device__ __forceinline__ void pk_decide(const uint32_t *__restrict__ Bsm, const uint32_t *__restrict__ T256,
                                           const uint32_t *__restrict__ Psm, const SweepArgs &a, int p,
                                           uint32_t c1, uint32_t c3, PkItem &it) {
@@ -310,14 +347,16 @@ __device__ __forceinline__ void pk_decide(const uint32_t *__restrict__ Bsm, cons
     const uint32_t hb = (b & 0xFEFEFEFEu) | (par * 0x01010101u);
     const uint32_t mb = (hb ^ (smask * 0xFFu)) + smask;
     const uint32_t uw = word_of(philox10(make_uint4(vid, c1 >> 2, (uint32_t)a.k, c3), a.key0, a.key1), c1 & 3u);
-    uint32_t acc = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
-        const bool ok = (idx <= 128u) || accept_by_top_byte((uw >> (8 * q)) & 0xFFu, T256[idx], vid, 4u * c1 + q,
-                                                            (uint32_t)a.k, c3, a.key0, a.key1);
-        acc |= (uint32_t)ok << q;
-    }
+    // The four decisions in 16-bit lanes, as in the multi-spin-coded item.
+    const uint32_t e0 = T256[mb & 0xFFu], e1 = T256[(mb >> 8) & 0xFFu];
+    const uint32_t e2 = T256[(mb >> 16) & 0xFFu], e3 = T256[mb >> 24];
+    const uint32_t slo = __byte_perm(uw, 0u, 0x4140u) * 128u + __byte_perm(e0, e1, 0x5410u);
+    const uint32_t shi = __byte_perm(uw, 0u, 0x4342u) * 128u + __byte_perm(e2, e3, 0x5410u);
+    const uint32_t RT = prmt_sign(slo, shi, 0xFDB9u);                               // reject or tie
+    const uint32_t RS = prmt_sign(slo - 0x00010001u, shi - 0x00010001u, 0xFDB9u);   // reject
+    uint32_t acc = (((~RT >> 7) & 0x01010101u) * 0x01020408u) >> 24;       // bit q: replica q accepted
+    uint32_t tie = ((((RT & ~RS) >> 7) & 0x01010101u) * 0x01020408u) >> 24;
+    if (tie) acc = pk_settle_ties(a, acc, tie, mb, vid, c1, c3);   // rare
     it.b = b;
     it.mb = mb;
     it.smask = smask;
@@ -384,7 +423,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
     const int nsweeps = act ? a.S : 0;
     const int np = a.g.np;
     uint32_t *Bsm = reinterpret_cast<uint32_t *>(smem);          // [np + 32], last 32 are scratch
-    uint32_t *T256 = Bsm + np + 32;                                 // [256] by m + 128
+    uint32_t *T256 = Bsm + np + 32;                                 // [256] decision entries by m + 128
     int32_t *cls = reinterpret_cast<int32_t *>(T256 + 256);
     const int csz = (a.g.ncol + 1 + 3) & ~3;
     int32_t *Eacc = cls + csz;      // [4]
@@ -397,10 +436,7 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     uint2 *Q = Qall + (size_t)(tid >> 5) * PK_QCAP;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
-    for (int i = tid; i < 256; i += NT) {
-        const int m = i - 128;
-        T256[i] = (m >= 1 && m <= a.g.mmax) ? tab[m] : 0u;
-    }
+    for (int i = tid; i < 256; i += NT) T256[i] = msc_entry(i, false, tab, a.g.mmax);   // by m + 128
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
     for (int i = tid; i < npw; i += NT) Psm[i] = a.g.parity[i];
 
@@ -576,14 +612,6 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_packed(const SweepArgs a) {
 // are queued and settled by all 32 lanes together before the class barrier
 // (one tail Philox call per lane instead of one per tying lane while the
 // others wait). Accepted replicas flip with one XOR.
-// Byte permute with sign replication: each selector nibble with bit 3 set
-// fills its result byte with the top bit of the selected byte.
-__device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
 __device__ __forceinline__ int msc_bit(int r) {   // bit of replica r = 4g + q in a word
     return 8 * (r & 3) + (r >> 2);
 }
@@ -748,18 +776,6 @@ __device__ __forceinline__ void msc_csa4(uint32_t (&pl)[NPL], uint32_t x, uint32
         pl[b] ^= k;
         k = carry;
     }
-}
-
-// Entry i of the decision table: E(m) in both 16-bit halves, m = i - 32 for
-// counts of |m| <= 31 (byte offset 4m + 128), else m = i - 128 (word index).
-__device__ __forceinline__ uint32_t msc_entry(int i, bool pk, const uint32_t *tab, int mmax) {
-    const int m = pk ? i - 32 : i - 128;
-    uint32_t e = 1u;   // m <= 0: always accepted
-    if (m > 0) {
-        const uint32_t T = m <= mmax ? tab[m] : 0u;
-        e = T == 0u ? 0x8040u : 0x8000u - 128u * (T >> 24) + ((T & 0xFFFFFFu) == 0u ? 64u : 0u);
-    }
-    return e * 0x00010001u;
 }
 
 template <int NPL, bool WEIGHTED>
@@ -1209,10 +1225,12 @@ void *msc_kernel(int mmax) {
 template <bool W>
 void *packed_kernel(int threads) {
     switch (threads) {
-        case 128: return reinterpret_cast<void *>(&k_sweep_packed<W, 128, 12>);
-        case 256: return reinterpret_cast<void *>(&k_sweep_packed<W, 256, 6>);
-        case 384: return reinterpret_cast<void *>(&k_sweep_packed<W, 384, 4>);
-        case 512: return reinterpret_cast<void *>(&k_sweep_packed<W, 512, 3>);
+        // 64 registers a thread (at least 1024 threads per SM): the packed item
+        // with its lane decisions spills at 40 registers.
+        case 128: return reinterpret_cast<void *>(&k_sweep_packed<W, 128, 8>);
+        case 256: return reinterpret_cast<void *>(&k_sweep_packed<W, 256, 4>);
+        case 384: return reinterpret_cast<void *>(&k_sweep_packed<W, 384, 2>);
+        case 512: return reinterpret_cast<void *>(&k_sweep_packed<W, 512, 2>);
         default: return reinterpret_cast<void *>(&k_sweep_packed<W, 1024, 1>);
     }
 }
