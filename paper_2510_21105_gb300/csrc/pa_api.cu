@@ -578,7 +578,8 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
         return fail(c, PA_EINVAL, "K, R (1..65536) or sweeps out of range");
     if (int rc = validate_opts(c, o)) return rc;
     if (o.nlm_period > 0 && o.nlm_kind == 0 && pa::nlm_smem_bytes(c->np) > 200 * 1024)
-        return fail(c, PA_EINVAL, "non-local moves support n <= 32768");
+        return fail(c, PA_EINVAL, "Houdayer moves need " + std::to_string(pa::nlm_smem_bytes(c->np)) +
+                                      " bytes of shared memory per replica pair, more than 200 KB");
     if (!o.adaptive) {
         if (K > 0 && !betas) return fail(c, PA_EINVAL, "betas is NULL");
         double prev = 0.0;

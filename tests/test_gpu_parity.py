@@ -98,6 +98,19 @@ def test_parity_nonlocal_moves(variant):
 
 
 @pytest.mark.parametrize("variant", [0, 1, 3])
+@pytest.mark.parametrize("n,m", [(600, 900), (300, 3000)])
+def test_parity_nonlocal_moves_low_and_high_degree(variant, n, m):
+    """Houdayer moves on graphs of mean degree 3 (rows shorter than the group
+    of 4 lanes that reads one) and 20 (five passes per row)."""
+    g = wl.gnm(n, m, seed=n + m)
+    betas = wl.linear_betas(0.1, 3.0, 9)
+    gpu = run_gpu(g, betas, 128, 2, seed=17, nlm_period=2, variant=variant)
+    orc = run_oracle(g, betas, 128, 2, seed=17, nlm_period=2)
+    assert orc.step_nlm_pairs.sum() > 0 and orc.step_nlm_flips.sum() > 0
+    assert_parity(gpu, orc, g, 128, 2)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 3])
 def test_parity_nonlocal_moves_signed(variant):
     """Houdayer moves on a +-1 torus: the multi-spin-coded layouts update the
     two energies from the bonds across the cluster boundary, the others
@@ -305,18 +318,18 @@ def test_parity_msc_many_words_ragged_last_word(variant):
 def test_parity_largest_graph_that_fits_shared_memory():
     """n = 40000: too large for the packed (n <= 32720) and int16 layouts, so
     AUTO falls back to multi-spin coding even with fewer words than SMs; block
-    moves run at this size (Houdayer moves need n <= 32768 and are refused)."""
+    moves and Houdayer moves (bitsets of both replicas and the candidates, a
+    16-bit queue: 95 KB of shared memory per pair) both run at this size."""
     g = wl.gnm(40000, 60000, seed=61)
     betas = wl.linear_betas(0.2, 1.5, 3)
     gpu = run_gpu(g, betas, 40, 1, seed=3, nlm_period=2, nlm_kind=1, nlm_block=8)
     assert gpu["stats"]["variant"] == 1
     orc = run_oracle(g, betas, 40, 1, seed=3, nlm_period=2, nlm_kind=1, nlm_block=8)
     assert_parity(gpu, orc, g, 40, 1)
-    a = B.Annealer.from_graph(g)
-    with pytest.raises(B.PaError) as e:
-        a.begin(betas, R=40, S=1, seed=3, nlm_period=2)
-    assert e.value.code == B.PA_EINVAL
-    a.close()
+    gpu = run_gpu(g, betas, 40, 1, seed=3, nlm_period=2)
+    assert gpu["stats"]["variant"] == 1
+    orc = run_oracle(g, betas, 40, 1, seed=3, nlm_period=2)
+    assert_parity(gpu, orc, g, 40, 1)
 
 
 def test_layouts_that_do_not_fit_are_refused():
