@@ -231,7 +231,7 @@ def run_reference(args, rank, world):
 # tail launches of the multi-spin-coded sweep, or the one launch of another
 # layout), from one ncu capture, with the SHA-256 prefix of the sweep source it
 # was taken on: reported only while that source is the one that runs.
-SWEEP_TRAFFIC = {"k_sweep_msc+pair": ((102.873600 + 41.293056 + 12.874496) * 1e6, "4f5d6dab7dc7f9b5")}
+SWEEP_TRAFFIC = {"k_sweep_msc+pair": ((102.910976 + 44.920832 + 12.874240) * 1e6, "9d6a8d2033bee303")}
 SWEEP_SRC = os.path.join(ROOT, "paper_2510_21105_gb300", "csrc", "k_sweep.cu")
 INT_LANES_PER_SM = 128   # ALU pipe 64 + FMA pipe 64 integer lanes per SM and clock (unit counts)
 SMEM_BYTES_PER_SM = 128  # shared-memory bytes per SM and clock (32 banks x 4 B)
@@ -251,13 +251,13 @@ def msc_ops_per_attempt(mean_degree: float) -> float:
       count bytes     8 x 8 bit transpose in every byte lane: 12 swaps x 4 ops
       uniforms        2 Philox4x32-10 calls x 10 rounds x (2 widening
                       multiplies + 2 three-input xors)
-      decisions       per 4-replica group: 4 index extracts, 2 entry merges,
+      decisions       per 4-replica group: 2 pair-table offsets (dot products),
                       2 uniform spreads, 2 multiply-adds, 2 subtracts, 2 sign
                       permutes, 2 mask merges
       energies        per group: table index, count byte, masked select, add
     Loads, addressing, loop control, barriers and the row packing at load and
     store are not counted."""
-    per_item = 4.5 * mean_degree + 12 * 4 + 2 * 10 * 4 + 8 * 16 + 8 * 4
+    per_item = 4.5 * mean_degree + 12 * 4 + 2 * 10 * 4 + 8 * 12 + 8 * 4
     return per_item / 32.0
 
 

@@ -700,6 +700,27 @@ struct MscPackedE {
     static constexpr bool value = NPL <= 5;
 };
 
+// Pair decision table of the packed-energy items: entry (m0 + H/2) + H (m1 + H/2)
+// holds E(m0) in its low and E(m1) in its high 16-bit lane, H = 2^(NPL+1)
+// (|m| < H/2). One load decides two replicas; the byte offset of the entry
+// is one dot product of the item's index bytes 4(m + H/2) with (1, H).
+template <int NPL>
+struct MscPairTab {
+    static constexpr int H = 2 << NPL;
+    static constexpr int words = MscPackedE<NPL>::value ? H * H : 0;
+};
+
+__host__ __device__ inline int msc_pair_words(int mmax) {
+    return mmax <= 7 ? 256 : mmax <= 15 ? 1024 : mmax <= 31 ? 4096 : 0;
+}
+
+template <int NPL>
+__device__ __forceinline__ void msc_fill_pair_table(uint32_t *PT, const uint32_t *T256, int tid, int NT) {
+    constexpr int H = MscPairTab<NPL>::H;
+    for (int i = tid; i < MscPairTab<NPL>::words; i += NT)
+        PT[i] = (T256[i % H - H / 2 + 32] & 0xFFFFu) | (T256[i / H - H / 2 + 32] & 0xFFFF0000u);
+}
+
 __device__ __forceinline__ void msc_flush_energy(uint32_t (&ebias)[8], int &cnt, int32_t *Eacc, int lane) {
     const int nwarp = (int)__reduce_add_sync(0xFFFFFFFFu, (uint32_t)cnt);
     uint32_t mine = 0;
@@ -831,7 +852,8 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
         }
     }
     constexpr bool PK = MscPackedE<NPL>::value;
-    const uint32_t base = PK ? 128u - 4u * deg : 128u - deg;   // mb byte = 4m + 128 (PK, deg <= 31) or m + 128
+    constexpr uint32_t H = (uint32_t)MscPairTab<NPL>::H;
+    const uint32_t base = PK ? 2u * H - 4u * deg : 128u - deg;   // mb byte = 4(m + H/2) (PK) or m + 128
     // Both Philox calls of the item (slots 32 blk .. +15 and +16 .. +31).
     uint4 u0, u1;
     philox_from_shared2(philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1), 2u * blk, 2u * blk + 1u, a.key0,
@@ -866,14 +888,20 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
         const uint32_t mb = r[g] * (PK ? 8u : 2u) + base * 0x01010101u;
         const uint4 &uq = g < 4 ? u0 : u1;
         const uint32_t uw = (g & 3) == 0 ? uq.x : (g & 3) == 1 ? uq.y : (g & 3) == 2 ? uq.z : uq.w;
-        uint32_t e[4];
+        uint32_t e01, e23;
+        if (PK) {   // byte offsets of the pair entries: b0 + H b1 and b2 + H b3 of the bytes b = 4(m + H/2)
+            e01 = *reinterpret_cast<const uint32_t *>(tb + __dp4a(mb, 0x00000001u | (H << 8), 0u));
+            e23 = *reinterpret_cast<const uint32_t *>(tb + __dp4a(mb, 0x00010000u | (H << 24), 0u));
+        } else {
+            uint32_t e[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const uint32_t idx = (mb >> (8 * q)) & 0xFFu;
-            e[q] = *reinterpret_cast<const uint32_t *>(tb + (PK ? idx : 4u * idx));
+            for (int q = 0; q < 4; ++q)
+                e[q] = *reinterpret_cast<const uint32_t *>(tb + 4u * ((mb >> (8 * q)) & 0xFFu));
+            e01 = __byte_perm(e[0], e[1], 0x5410u);
+            e23 = __byte_perm(e[2], e[3], 0x5410u);
         }
-        const uint32_t slo = __byte_perm(uw, 0u, 0x4140u) * 128u + __byte_perm(e[0], e[1], 0x5410u);
-        const uint32_t shi = __byte_perm(uw, 0u, 0x4342u) * 128u + __byte_perm(e[2], e[3], 0x5410u);
+        const uint32_t slo = __byte_perm(uw, 0u, 0x4140u) * 128u + e01;
+        const uint32_t shi = __byte_perm(uw, 0u, 0x4342u) * 128u + e23;
         const uint32_t RT = prmt_sign(slo, shi, 0xFDB9u);                               // reject or tie
         const uint32_t RS = prmt_sign(slo - 0x00010001u, shi - 0x00010001u, 0xFDB9u);   // reject
         const uint32_t M = 0x01010101u << g;
@@ -969,7 +997,8 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     const int nsweeps = act ? a.S : 0;
     const int np = a.g.np, n = a.g.n;
     uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] decision table (see above)
-    uint32_t *Wsm = T256 + 256;                                     // [np]
+    uint32_t *PT = T256 + 256;                                      // [H * H] pair table (packed energies)
+    uint32_t *Wsm = PT + MscPairTab<NPL>::words;                    // [np]
     int32_t *cls = reinterpret_cast<int32_t *>(Wsm + np);
     const int csz = (a.g.ncol + 1 + 3) & ~3;
     int32_t *Eacc = cls + csz;      // [32]
@@ -980,6 +1009,10 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
     for (int i = tid; i < 256; i += NT) T256[i] = msc_entry(i, MscPackedE<NPL>::value, tab, a.g.mmax);
+    if (MscPackedE<NPL>::value) {
+        __syncthreads();
+        msc_fill_pair_table<NPL>(PT, T256, tid, NT);
+    }
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
 
     for (int lb = blockIdx.x; lb < a.nblk; lb += gridDim.x) {
@@ -1018,7 +1051,8 @@ __global__ void __launch_bounds__(NTB, MINB) k_sweep_msc(const SweepArgs a) {
                     if (p < p1) {
                         const uint32_t x = Wsm[p];
                         const uint32_t acc32 =
-                            msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, Eacc, ebias, tent);
+                            msc_item<NPL, WEIGHTED>(a, Wsm, MscPackedE<NPL>::value ? PT : T256, p, x, c3, blk, Eacc,
+                                                    ebias, tent);
                         if (acc32) {
                             Wsm[p] = x ^ acc32;
                             nacc += __popc(acc32 & vmask);
@@ -1093,7 +1127,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
     const int nsweeps = act ? a.S : 0;
     const int np = a.g.np, n = a.g.n;
     uint32_t *T256 = reinterpret_cast<uint32_t *>(smem);          // [256] decision table (see above)
-    uint32_t *Wsm = T256 + 256;                                     // [np]
+    uint32_t *PT = T256 + 256;                                      // [H * H] pair table (packed energies)
+    uint32_t *Wsm = PT + MscPairTab<NPL>::words;                    // [np]
     int32_t *cls = reinterpret_cast<int32_t *>(Wsm + np);
     const int csz = (a.g.ncol + 1 + 3) & ~3;
     int32_t *Eacc = cls + csz;      // [32] (used in CTA 0)
@@ -1106,6 +1141,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
     const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31;
     const uint32_t *tab = a.tables + (size_t)a.tidx[a.k] * (a.g.mmax + 1);
     for (int i = tid; i < 256; i += NT) T256[i] = msc_entry(i, MscPackedE<NPL>::value, tab, a.g.mmax);
+    if (MscPackedE<NPL>::value) {
+        __syncthreads();
+        msc_fill_pair_table<NPL>(PT, T256, tid, NT);
+    }
     for (int i = tid; i <= a.g.ncol; i += NT) cls[i] = a.g.cls[i];
 
     const int ncl = (int)(gridDim.x >> 1);
@@ -1143,7 +1182,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(256, 4) k_sweep_msc_
                     uint32_t tent = 0u;
                     if (p < p1) {
                         const uint32_t x = Wsm[p];
-                        const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, T256, p, x, c3, blk, E0, ebias, tent);
+                        const uint32_t acc32 = msc_item<NPL, WEIGHTED>(a, Wsm, MscPackedE<NPL>::value ? PT : T256, p, x, c3,
+                                                                       blk, E0, ebias, tent);
                         if (acc32) {
                             Wsm[p] = x ^ acc32;
                             Wpeer[p] = x ^ acc32;
@@ -1256,7 +1296,8 @@ void *select_kernel(int G, int fb, bool weighted, int threads, int mmax) {
 
 size_t sweep_smem_bytes(const GraphDev &g, int G, int field_bits, int threads) {
     if (field_bits == 1 || field_bits == 2)   // multi-spin coded: 32 replicas per word (2: CTA pairs)
-        return (size_t)g.np * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + (32 + 32 + 8) * 4 +
+        return (size_t)g.np * 4 + (256 + (size_t)msc_pair_words(g.mmax)) * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 +
+               (32 + 32 + 8) * 4 +
                (size_t)(threads / 32) * 64 * 4;   // tie queues
     if (field_bits == 7)
         return (size_t)(g.np + 32) * 4 + 256 * 4 + (size_t)((g.ncol + 1 + 3) & ~3) * 4 + 16 * 4 +

@@ -18,8 +18,9 @@ def test_smem_bytes_per_attempt_by_layout():
 
 def test_msc_ops_per_attempt_counts_each_part():
     # per 32-replica item: 4.5 ops per bond, 48 for the count bytes, 80 for two
-    # Philox calls, 16 per 4-replica group for the decision and 4 for energies
-    assert bench.msc_ops_per_attempt(0.0) == pytest.approx((48 + 80 + 128 + 32) / 32)
+    # Philox calls, 12 per 4-replica group for the decision (two pair-table
+    # lookups) and 4 for energies
+    assert bench.msc_ops_per_attempt(0.0) == pytest.approx((48 + 80 + 96 + 32) / 32)
     assert bench.msc_ops_per_attempt(12.0) - bench.msc_ops_per_attempt(4.0) == pytest.approx(4.5 * 8 / 32)
 
 
