@@ -231,7 +231,7 @@ def run_reference(args, rank, world):
 # tail launches of the multi-spin-coded sweep, or the one launch of another
 # layout), from one ncu capture, with the SHA-256 prefix of the sweep source it
 # was taken on: reported only while that source is the one that runs.
-SWEEP_TRAFFIC = {"k_sweep_msc+pair": ((102.910976 + 44.920832 + 12.874240) * 1e6, "9d6a8d2033bee303")}
+SWEEP_TRAFFIC = {"k_sweep_msc+pair": ((102.907904 + 44.890112 + 12.868608) * 1e6, "7c93717a46171f76")}
 SWEEP_SRC = os.path.join(ROOT, "paper_2510_21105_gb300", "csrc", "k_sweep.cu")
 INT_LANES_PER_SM = 128   # ALU pipe 64 + FMA pipe 64 integer lanes per SM and clock (unit counts)
 SMEM_BYTES_PER_SM = 128  # shared-memory bytes per SM and clock (32 banks x 4 B)
@@ -244,20 +244,35 @@ def sweep_source_sha() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def msc_ops_per_attempt(mean_degree: float) -> float:
+def msc_planes(max_degree: int) -> int:
+    """Bit planes of the frustrated-bond counters (counts up to max_degree)."""
+    return 3 if max_degree <= 7 else 4 if max_degree <= 15 else 5 if max_degree <= 31 else 6 if max_degree <= 63 else 7
+
+
+def msc_ops_per_attempt(mean_degree: float, max_degree: int = 31) -> float:
     """Algorithmic integer instructions of one multi-spin-coded attempt: one
     item (one position of a 32-replica word) divided by its 32 attempts.
-      bond counting   18 three-input logic ops per 4 bonds (carry-save adders)
+      bond counting   per 4 bonds, three-input logic ops of the carry-save
+                      adders: 7 + 2 (NPL - 3) with the planes kept
+                      complemented (NPL >= 4), 13 with plain adders from
+                      zero (NPL = 3); NPL ops to decode the complemented form
       count bytes     8 x 8 bit transpose in every byte lane: 12 swaps x 4 ops
       uniforms        2 Philox4x32-10 calls x 10 rounds x (2 widening
                       multiplies + 2 three-input xors)
       decisions       per 4-replica group: 2 pair-table offsets (dot products),
                       2 uniform spreads, 2 multiply-adds, 2 subtracts, 2 sign
-                      permutes, 2 mask merges
+                      permutes, 2 mask merges (NPL <= 5; wider counts: 4 index
+                      extracts and 2 half-word merges instead of the offsets)
       energies        per group: table index, count byte, masked select, add
     Loads, addressing, loop control, barriers and the row packing at load and
     store are not counted."""
-    per_item = 4.5 * mean_degree + 12 * 4 + 2 * 10 * 4 + 8 * 12 + 8 * 4
+    npl = msc_planes(max_degree)
+    if npl >= 4:
+        bonds = (7 + 2 * (npl - 3)) / 4.0 * mean_degree + npl
+    else:
+        bonds = 13 / 4.0 * mean_degree
+    decisions = 8 * (12 if npl <= 5 else 16)
+    per_item = bonds + 12 * 4 + 2 * 10 * 4 + decisions + 8 * 4
     return per_item / 32.0
 
 
@@ -279,7 +294,8 @@ def smem_bytes_per_attempt(kernel, mean_degree, accept_rate):
     return 2.0 + 4.0 + accept_rate * 2.0 * mean_degree
 
 
-def sweep_roofline(stats, attempts_per_launch, probe, clk_mhz, kernel, mean_degree, accept_rate, sms=SMS):
+def sweep_roofline(stats, attempts_per_launch, probe, clk_mhz, kernel, mean_degree, accept_rate, sms=SMS,
+                   max_degree=31):
     """Roofline of the sweep (the dominant kernel): integer-issue bound.
     probe: pa_probe_peaks of the device (measured peaks) or None."""
     launches = max(stats["sweep_launches"], 1)
@@ -288,7 +304,7 @@ def sweep_roofline(stats, attempts_per_launch, probe, clk_mhz, kernel, mean_degr
         return None
     aps = attempts_per_launch / t
     msc = kernel[0].startswith("k_sweep_msc")
-    ops = msc_ops_per_attempt(mean_degree) if msc else packed_ops_per_attempt(mean_degree, accept_rate)
+    ops = msc_ops_per_attempt(mean_degree, max_degree) if msc else packed_ops_per_attempt(mean_degree, accept_rate)
     achieved = aps * ops / 1e12
     derived = sms * INT_LANES_PER_SM * clk_mhz * 1e6 / 1e12
     peak = probe["int_ops_per_s"] / 1e12 if probe else derived
@@ -403,7 +419,7 @@ def run_ours(args, rank, world, dist):
     clocks = clk.summary()
     clk_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     roof = sweep_roofline(stats_acc, g.n * R * S, probe, clk_mhz, kernel, 2.0 * g.m / g.n, acc_rate,
-                          sms=probe["sms"])
+                          sms=probe["sms"], max_degree=int(g.maxdeg))
     ann.close()
 
     # end to end through the C-ABI with host buffers (pinned), copies inside the region

@@ -738,33 +738,32 @@ __device__ __forceinline__ void msc_flush_energy(uint32_t (&ebias)[8], int &cnt,
 
 // Philox4x32-10 of two counters of one item (word 1 = c1a, c1b), finished
 // from the shared round-1-3 products and advanced round by round together,
-// so that the two dependency chains interleave. Round 1: only word 0 depends
+// so that the two dependency chains interleave. The round keys come
+// precomputed in the kernel arguments (rk0[r] = key0 + r * 0x9E3779B9,
+// rk1[r] = key1 + r * 0xBB67AE85), so they are operands, not additions. Round 1: only word 0 depends
 // on c1. Round 2: the word-2 product (s0, s1) is shared, the word-0 product
 // is per counter. Round 3: the word-0 product (h3, l3) is shared.
-__device__ __forceinline__ void philox_from_shared2(const PhiloxShared &p, uint32_t c1a, uint32_t c1b, uint32_t k0,
-                                                    uint32_t k1, uint4 &ra, uint4 &rb) {
+__device__ __forceinline__ void philox_from_shared2(const PhiloxShared &p, uint32_t c1a, uint32_t c1b,
+                                                    const uint32_t (&rk0)[10], const uint32_t (&rk1)[10], uint4 &ra,
+                                                    uint4 &rb) {
     uint32_t lo, hi, lo2, hi2;
     mul_wide(0xD2511F53u, p.u1 ^ c1a, lo, hi);
     mul_wide(0xD2511F53u, p.u1 ^ c1b, lo2, hi2);
-    uint4 a = make_uint4(p.s0, p.s1, hi ^ p.b ^ (k1 + 0xBB67AE85u), lo);
-    uint4 b = make_uint4(p.s0, p.s1, hi2 ^ p.b ^ (k1 + 0xBB67AE85u), lo2);
-    k0 += 2u * 0x9E3779B9u;
-    k1 += 2u * 0xBB67AE85u;
+    uint4 a = make_uint4(p.s0, p.s1, hi ^ p.b ^ rk1[1], lo);
+    uint4 b = make_uint4(p.s0, p.s1, hi2 ^ p.b ^ rk1[1], lo2);
     mul_wide(0xCD9E8D57u, a.z, lo, hi);
     mul_wide(0xCD9E8D57u, b.z, lo2, hi2);
-    a = make_uint4(hi ^ a.y ^ k0, lo, p.h3 ^ a.w ^ k1, p.l3);
-    b = make_uint4(hi2 ^ b.y ^ k0, lo2, p.h3 ^ b.w ^ k1, p.l3);
+    a = make_uint4(hi ^ a.y ^ rk0[2], lo, p.h3 ^ a.w ^ rk1[2], p.l3);
+    b = make_uint4(hi2 ^ b.y ^ rk0[2], lo2, p.h3 ^ b.w ^ rk1[2], p.l3);
 #pragma unroll
     for (int r = 3; r < 10; ++r) {
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
         uint32_t alo0, ahi0, alo1, ahi1, blo0, bhi0, blo1, bhi1;
         mul_wide(0xD2511F53u, a.x, alo0, ahi0);
         mul_wide(0xD2511F53u, b.x, blo0, bhi0);
         mul_wide(0xCD9E8D57u, a.z, alo1, ahi1);
         mul_wide(0xCD9E8D57u, b.z, blo1, bhi1);
-        a = make_uint4(ahi1 ^ a.y ^ k0, alo1, ahi0 ^ a.w ^ k1, alo0);
-        b = make_uint4(bhi1 ^ b.y ^ k0, blo1, bhi0 ^ b.w ^ k1, blo0);
+        a = make_uint4(ahi1 ^ a.y ^ rk0[r], alo1, ahi0 ^ a.w ^ rk1[r], alo0);
+        b = make_uint4(bhi1 ^ b.y ^ rk0[r], blo1, bhi0 ^ b.w ^ rk1[r], blo0);
     }
     ra = a;
     rb = b;
@@ -799,6 +798,30 @@ __device__ __forceinline__ void msc_csa4(uint32_t (&pl)[NPL], uint32_t x, uint32
     }
 }
 
+// Adds four bonds to counters kept in complemented form A_b = plane_b ^ x,
+// where the input words are the raw neighbour words w_j (= d_j ^ x). A full
+// adder keeps the form: (a^x) ^ (p^x) ^ (q^x) = (a^p^q) ^ x and, majority
+// being self-dual, maj(a^x, p^x, q^x) = maj(a, p, q) ^ x. So two full adders
+// take w0..w3 into the ones plane, one more takes their carries into the twos
+// plane, and half adders (a^p^x, ((a^x) & (p^x)) ^ x) ripple the single carry
+// upwards: 7 + 2 (NPL - 3) three-input logic ops per four bonds.
+template <int NPL>
+__device__ __forceinline__ void msc_step4x(uint32_t (&A)[NPL], uint32_t x, uint32_t w0, uint32_t w1, uint32_t w2,
+                                           uint32_t w3) {
+    const uint32_t c1 = (A[0] & w0) | (w1 & (A[0] | w0));
+    A[0] ^= w0 ^ w1;
+    const uint32_t c2 = (A[0] & w2) | (w3 & (A[0] | w2));
+    A[0] ^= w2 ^ w3;
+    uint32_t c = (A[1] & c1) | (c2 & (A[1] | c1));
+    A[1] ^= c1 ^ c2;
+#pragma unroll
+    for (int b = 2; b < NPL; ++b) {
+        const uint32_t nc = b + 1 < NPL ? (((A[b] ^ x) & (c ^ x)) ^ x) : 0u;
+        A[b] ^= c ^ x;
+        c = nc;
+    }
+}
+
 template <int NPL, bool WEIGHTED>
 __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t *Wsm, const uint32_t *T256, int p,
                                              uint32_t x, uint32_t c3, int blk, int32_t *Eacc,
@@ -814,6 +837,12 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
         const uint32_t h0 = __ldg(&a.g.mrp[p]), h1 = __ldg(&a.g.mrp[p + 1]);
         deg = h0 & 0xFFu;
         const unsigned char *Wb = reinterpret_cast<const unsigned char *>(Wsm);
+        // The planes in complemented form (msc_step4x). With NPL = 3 (degree <= 7,
+        // at most two steps) the plain adders starting from zero fold further
+        // and stay cheaper.
+        uint32_t A[NPL];
+#pragma unroll
+        for (int b = 0; b < NPL; ++b) A[b] = NPL >= 4 ? x : 0u;
         for (uint32_t q = h0 >> 8; q < (h1 >> 8); ++q) {
             const uint2 v = __ldg(&a.g.mcol[q]);
             const uint32_t o[4] = {v.x & 0xFFFFu, v.x >> 16, v.y & 0xFFFFu, v.y >> 16};
@@ -823,8 +852,11 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
                 w[j] = *reinterpret_cast<const uint32_t *>(Wb + (WEIGHTED ? (o[j] & ~3u) : o[j]));
                 if (WEIGHTED && (o[j] & 1u)) w[j] = ~w[j];
             }
-            msc_csa4<NPL>(pl, x, w[0], w[1], w[2], w[3]);
+            if (NPL >= 4) msc_step4x<NPL>(A, x, w[0], w[1], w[2], w[3]);
+            else msc_csa4<NPL>(A, x, w[0], w[1], w[2], w[3]);
         }
+#pragma unroll
+        for (int b = 0; b < NPL; ++b) pl[b] = NPL >= 4 ? A[b] ^ x : A[b];
     } else {
         const uint32_t e0 = __ldg(&a.g.rp[p]), e1 = __ldg(&a.g.rp[p + 1]);
         deg = e1 - e0;
@@ -856,8 +888,8 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
     const uint32_t base = PK ? 2u * H - 4u * deg : 128u - deg;   // mb byte = 4(m + H/2) (PK) or m + 128
     // Both Philox calls of the item (slots 32 blk .. +15 and +16 .. +31).
     uint4 u0, u1;
-    philox_from_shared2(philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1), 2u * blk, 2u * blk + 1u, a.key0,
-                        a.key1, u0, u1);
+    philox_from_shared2(philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1), 2u * blk, 2u * blk + 1u, a.rk0, a.rk1,
+                        u0, u1);
     // Byte q of r[g] = c of replica 4g + q: an 8 x 8 bit transpose in every byte lane.
     uint32_t r[8];
 #pragma unroll

@@ -859,6 +859,10 @@ int enqueue_step(pa_ctx *c, int32_t k, cudaStream_t st, bool time_sweep) {
     sa.k = k;
     sa.key0 = k0;
     sa.key1 = k1;
+    for (int r = 0; r < 10; ++r) {
+        sa.rk0[r] = k0 + (uint32_t)r * 0x9E3779B9u;
+        sa.rk1[r] = k1 + (uint32_t)r * 0xBB67AE85u;
+    }
     sa.best_rec = r.best_rec.as<int4>();
     sa.best_cfg = r.best_cfg.as<int8_t>();
     sa.accepts = r.rec_acc.as<unsigned long long>();

@@ -119,6 +119,7 @@ struct SweepArgs {
     int32_t R, nblk, S, k;       // nblk: replica blocks of this launch
     int32_t blk_base;            // first replica block of this launch (multi-spin-coded kernels)
     uint32_t key0, key1;
+    uint32_t rk0[10], rk1[10];   // Philox round keys key + r * (0x9E3779B9, 0xBB67AE85)
     int4 *best_rec;              // [all blocks] (E, step, sweep, slot) per replica block
     int8_t *best_cfg;            // [nblk][np] configuration of that record
     unsigned long long *accepts; // [K] accepted flips per step

@@ -17,11 +17,16 @@ def test_smem_bytes_per_attempt_by_layout():
 
 
 def test_msc_ops_per_attempt_counts_each_part():
-    # per 32-replica item: 4.5 ops per bond, 48 for the count bytes, 80 for two
-    # Philox calls, 12 per 4-replica group for the decision (two pair-table
-    # lookups) and 4 for energies
-    assert bench.msc_ops_per_attempt(0.0) == pytest.approx((48 + 80 + 96 + 32) / 32)
-    assert bench.msc_ops_per_attempt(12.0) - bench.msc_ops_per_attempt(4.0) == pytest.approx(4.5 * 8 / 32)
+    # per 32-replica item: 48 for the count bytes, 80 for two Philox calls, 12
+    # per 4-replica group for the decision (two pair-table lookups), 4 for
+    # energies; bonds: 11 ops per 4 bonds and 5 to decode with 5 planes
+    assert bench.msc_ops_per_attempt(0.0) == pytest.approx((5 + 48 + 80 + 96 + 32) / 32)
+    assert bench.msc_ops_per_attempt(12.0) - bench.msc_ops_per_attempt(4.0) == pytest.approx(11 / 4 * 8 / 32)
+    # 3 planes (degree <= 7): 13 ops per 4 bonds, nothing to decode
+    assert bench.msc_ops_per_attempt(4.0, 4) == pytest.approx((13 + 48 + 80 + 96 + 32) / 32)
+    # 7 planes: 15 ops per 4 bonds, single-entry decisions (16 per group)
+    assert bench.msc_ops_per_attempt(0.0, 100) == pytest.approx((7 + 48 + 80 + 128 + 32) / 32)
+    assert [bench.msc_planes(d) for d in (4, 7, 8, 15, 16, 31, 32, 63, 64, 127)] == [3, 3, 4, 4, 5, 5, 6, 6, 7, 7]
 
 
 def test_sweep_roofline_fractions():
