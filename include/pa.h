@@ -117,6 +117,16 @@ typedef struct {
                                  do not advance resample with q = 1 (identity).
                                  0 = off (default) */
     int32_t reheat_back;      /* entries a reheat steps back (>= 1) */
+    int32_t msc_no_split;     /* PA_VARIANT_MSC: 0 (default) = when the
+                                 32-replica words are more than, and not a
+                                 multiple of, the SMs, the first
+                                 (words / SMs) * SMs words run in one-CTA
+                                 blocks and the rest concurrently in CTA pairs
+                                 on a second stream, so that every SM carries
+                                 the same work; 1 = every word in one-CTA
+                                 blocks, for callers whose other work (a
+                                 batch, a loaded server) fills the SMs anyway.
+                                 Results do not depend on it. */
 } pa_anneal_opts;
 
 typedef struct {

@@ -67,8 +67,11 @@ def tune(g, betas, R, S, seed=0, steps=2, cache_path=None, candidates=None, cont
     if context != "alone":
         # The CTA-pair kernel only gains by balancing one instance over the SMs;
         # when other work fills the GPU that balance comes for free and its
-        # cluster barriers are pure cost.
+        # cluster barriers are pure cost. For the same reason the multi-spin-
+        # coded layout runs every word in one-CTA blocks (msc_no_split), which
+        # a timing of the instance alone cannot show.
         cands = [c for c in cands if c.get("variant") != 3] or cands
+        cands = [dict(c, msc_no_split=1) if c.get("variant") == 1 else c for c in cands]
     mid = max(0, len(betas) // 2 - steps)
     sl = list(betas[mid:mid + steps + 1])
     times = {}

@@ -36,7 +36,8 @@ class pa_anneal_opts(C.Structure):
                 ("replicas_per_cta", C.c_int32), ("threads_per_cta", C.c_int32),
                 ("stream", C.c_void_p), ("record_counts", C.c_int32), ("time_kernels", C.c_int32),
                 ("nlm_kind", C.c_int32), ("nlm_block", C.c_int32), ("acc_lo", C.c_double),
-                ("acc_hi", C.c_double), ("reheat_after", C.c_int32), ("reheat_back", C.c_int32)]
+                ("acc_hi", C.c_double), ("reheat_after", C.c_int32), ("reheat_back", C.c_int32),
+                ("msc_no_split", C.c_int32)]
 
 
 class pa_stats_t(C.Structure):

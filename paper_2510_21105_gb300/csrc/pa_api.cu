@@ -277,6 +277,7 @@ int validate_opts(pa_ctx *c, const pa_anneal_opts &o) {
     if (o.reheat_after < 0) return fail(c, PA_EINVAL, "reheat_after < 0");
     if (o.reheat_after > 0 && o.adaptive) return fail(c, PA_EINVAL, "reheating needs a fixed schedule");
     if (o.reheat_after > 0 && o.reheat_back < 1) return fail(c, PA_EINVAL, "reheat_back must be >= 1");
+    if (o.msc_no_split != 0 && o.msc_no_split != 1) return fail(c, PA_EINVAL, "msc_no_split must be 0 or 1");
     if (o.adaptive) {
         if (!(o.rho > 0.0 && o.rho <= 1.0)) return fail(c, PA_EINVAL, "rho must be in (0, 1]");
         if (o.adapt_J < 0 || o.adapt_J > 20) return fail(c, PA_EINVAL, "adapt_J must be 0..20");
@@ -615,7 +616,7 @@ int pa_anneal_begin(pa_ctx *c, const double *betas, int32_t K, int32_t R, int32_
     r.nblk = r.Rpad / (4 * G);
     r.nrec = r.nblk;
     r.split = false;
-    if (o.variant == PA_VARIANT_MSC) {
+    if (o.variant == PA_VARIANT_MSC && !o.msc_no_split) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1368,7 +1369,7 @@ int pa_save(pa_ctx *c, const char *path) {
     RunState &r = c->run;
     if (!r.begun) return fail(c, PA_ESTATE, "no anneal");
     CkptHeader h{};
-    std::memcpy(h.magic, "PAMCCKP2", 8);
+    std::memcpy(h.magic, "PAMCCKP3", 8);
     h.graph_hash = c->graph_hash;
     h.n = c->n;
     h.R = r.R;
@@ -1412,7 +1413,7 @@ int pa_load(pa_ctx *c, const char *path) {
     if (!f) return fail(c, PA_EINVAL, "cannot open checkpoint");
     CkptHeader h{};
     int32_t nb = 0;
-    bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, "PAMCCKP2", 8) == 0 &&
+    bool ok = std::fread(&h, sizeof(h), 1, f) == 1 && std::memcmp(h.magic, "PAMCCKP3", 8) == 0 &&
               std::fread(&nb, 4, 1, f) == 1 && nb >= 0 && nb <= (1 << 26);
     if (!ok || h.graph_hash != c->graph_hash || h.n != c->n) {
         std::fclose(f);

@@ -20,6 +20,7 @@ def _jobs():
         (wl.gnm(800, 3000, seed=5), None, 32, 2, 9,
          dict(adaptive=1, rho=0.5, adapt_J=4, adapt_dbeta_max=0.3, beta_max=1.5)),
         (wl.gnp(150, 0.1, seed=6), wl.linear_betas(0.3, 1.0, 3), 7, 1, 10, dict(field_bits=8)),
+        (wl.gnm(600, 3600, seed=7), wl.linear_betas(0.1, 2.5, 6), 5000, 2, 11, dict(variant=1, msc_no_split=1)),
     ]
 
 

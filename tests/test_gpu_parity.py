@@ -303,14 +303,15 @@ def test_repeat_runs_are_identical_and_launch_shape_free():
         assert np.array_equal(r1["spins"], r["spins"]) and r1["best"] == r["best"]
 
 
-@pytest.mark.parametrize("variant", [1, 3])
-def test_parity_msc_many_words_ragged_last_word(variant):
+@pytest.mark.parametrize("variant,extra", [(1, {}), (1, {"msc_no_split": 1}), (3, {})])
+def test_parity_msc_many_words_ragged_last_word(variant, extra):
     # R = 4937: 155 words of 32 replicas (more words than SMs, so blocks loop
     # over words) with 9 live replicas in the last one; signed weights and
-    # non-local moves.
+    # non-local moves. On 152 SMs the one-CTA layout splits the words 152 + 3
+    # over two kernels unless msc_no_split asks for one.
     g = wl.from_edges(300, *_random_edges(300, 1500, seed=99))
     betas = wl.linear_betas(0.1, 2.5, 6)
-    gpu = run_gpu(g, betas, 4937, 2, seed=31, variant=variant, nlm_period=2)
+    gpu = run_gpu(g, betas, 4937, 2, seed=31, variant=variant, nlm_period=2, **extra)
     orc = run_oracle(g, betas, 4937, 2, seed=31, nlm_period=2)
     assert_parity(gpu, orc, g, 4937, 2)
 
