@@ -5,6 +5,8 @@
         [--nlm-period P] [--nlm-kind 0|1] [--nlm-block B] [--variant 0|1|2] [--field-bits 16|8|7]
         [--replicas-per-cta 4|8] [--threads T] [--hex] [--save-hex FILE]
         [--curve FILE] [--checkpoint FILE --checkpoint-every K] [--resume FILE]
+        [--adaptive 1|2 [--rho F] [--adapt-J J] [--dbeta-max D] [--beta-max B] [--acc-lo F --acc-hi F]]
+        [--reheat-after Q --reheat-back N]
 
     python -m paper_2510_21105_gb300.cli verify --graph FILE --hex-file FILE
         [--expect-cut C]
@@ -16,6 +18,12 @@ hexadecimal format (Sec. 3) and --save-hex writes it to a file. A --graph
 file is in the G-set text format ("n m", then "i j w" per edge, 1-based);
 its schedule defaults to R=16384, S=10, beta 0.1 -> 4.0 over K=1000 steps,
 non-local moves every 50 steps.
+
+--adaptive 1 chooses each temperature step by the ESS rule, --adaptive 2
+by the acceptance-rate rule (both on the grid of --dbeta-max / 2^J up to
+--beta-max, with --steps / K as the cap), and --reheat-after steps back the
+fixed schedule after that many steps without a lower energy (the adaptive
+control options of pa_anneal_opts).
 
 For long runs, --checkpoint/--checkpoint-every save the whole anneal every K
 steps and --resume continues one (bit-exact: all randomness is counter based,
@@ -93,6 +101,16 @@ def _anneal(argv):
     p.add_argument("--checkpoint", default=None, help="checkpoint file written during the run")
     p.add_argument("--checkpoint-every", type=int, default=0, help="steps between checkpoints")
     p.add_argument("--resume", default=None, help="continue the anneal saved in this checkpoint")
+    p.add_argument("--adaptive", type=int, default=0,
+                   help="0 fixed schedule, 1 ESS-adaptive steps, 2 acceptance-rate-adaptive steps")
+    p.add_argument("--rho", type=float, default=0.5, help="adaptive 1: target ESS / R")
+    p.add_argument("--adapt-J", type=int, default=8, help="adaptive: finest grid level")
+    p.add_argument("--dbeta-max", type=float, default=0.05, help="adaptive: coarsest step")
+    p.add_argument("--beta-max", type=float, default=None, help="adaptive: final beta (default: the schedule's end)")
+    p.add_argument("--acc-lo", type=float, default=0.05, help="adaptive 2: lower acceptance bound")
+    p.add_argument("--acc-hi", type=float, default=0.25, help="adaptive 2: upper acceptance bound")
+    p.add_argument("--reheat-after", type=int, default=0, help="fixed schedules: stagnant steps before a reheat")
+    p.add_argument("--reheat-back", type=int, default=1, help="schedule entries a reheat steps back")
     a = p.parse_args(argv)
     build_mod.build()
     if a.graph:
@@ -118,9 +136,15 @@ def _anneal(argv):
             K = ann.K if a.steps is None else min(a.steps, ann.K)
             done = B.pa_run_info(ann.ctx)["steps_done"]
         else:
-            ann.begin(betas, c["R"], c["S"], c["seed"], nlm_period=c["nlm_period"], field_bits=a.field_bits,
-                      replicas_per_cta=a.replicas_per_cta, threads_per_cta=a.threads, variant=a.variant,
-                      nlm_kind=a.nlm_kind, nlm_block=a.nlm_block)
+            ctl = dict(reheat_after=a.reheat_after, reheat_back=a.reheat_back)
+            if a.adaptive:
+                ctl = dict(adaptive=a.adaptive, rho=a.rho, adapt_J=a.adapt_J, adapt_dbeta_max=a.dbeta_max,
+                           beta_max=a.beta_max if a.beta_max is not None else c["beta"][1],
+                           acc_lo=a.acc_lo, acc_hi=a.acc_hi)
+            ann.begin(None if a.adaptive else betas, c["R"], c["S"], c["seed"], K=c["K"],
+                      nlm_period=c["nlm_period"], field_bits=a.field_bits, replicas_per_cta=a.replicas_per_cta,
+                      threads_per_cta=a.threads, variant=a.variant, nlm_kind=a.nlm_kind, nlm_block=a.nlm_block,
+                      **ctl)
             done = 0
         every = a.checkpoint_every if a.checkpoint and a.checkpoint_every > 0 else max(K - done, 1)
         while done < K:
@@ -142,7 +166,8 @@ def _anneal(argv):
                 f.write("step,beta,t_ms,best_cut\n")
                 for k in range(len(ss["beta"])):
                     f.write(f"{k},{ss['beta'][k]:.17g},{ss['t_ms'][k]:.3f},{(W - int(best[k])) // 2}\n")
-    out = dict(config=name, n=g.n, m=g.m, R=c["R"], S=c["S"], steps=K, seed=c["seed"], best_cut=cut,
+    out = dict(config=name, n=g.n, m=g.m, R=c["R"], S=c["S"], steps=int(st["steps_run"]), seed=c["seed"],
+               best_cut=cut,
                best_step=step, best_sweep=sweep, wall_s=dt, attempts=st["attempts"],
                nlm_moves=int(ss_nlm[0]), nlm_flips=int(ss_nlm[1]),
                accepts=st["accepts"], device_ms=st["anneal_ms"], time_to_best_ms=st["t_best_ms"],

@@ -410,62 +410,45 @@ __global__ void __launch_bounds__(256) k_nlm_block(NlmArgs a) {
 }
 
 // -------------------------------------------------------------- adaptive ---
-__global__ void k_ad_partials(AdaptArgs a) {
+// ESS partials, one CTA per (256-slot chunk, level j): w = q_j^(E - E_min) by
+// squarings and w*w for one slot per thread, then the chunk's pairwise tree
+// sums (lanes by butterflies, then the eight warp sums in pairs), the same
+// additions as the tree over the whole padded population.
+__global__ void __launch_bounds__(RS_CHUNK) k_ad_partials(AdaptArgs a) {
     const int n_prev = a.state[0];
     if (n_prev >= a.nmax) return;
-    __shared__ double sw[2][RS_THREADS / 32];
-    const int emin = a.emin[a.k];
-    const int base = blockIdx.x * RS_CHUNK + threadIdx.x * 4;
-    uint32_t d[4];
-    bool valid[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        valid[q] = base + q < a.R;
-        d[q] = valid[q] ? (uint32_t)(a.E[base + q] - emin) : 0u;
-    }
+    __shared__ double sw[2][RS_CHUNK / 32];
+    const int j = blockIdx.y;
+    const int slot = blockIdx.x * RS_CHUNK + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int j = 0; j <= a.J; ++j) {
-        int dn = 1 << (a.J - j);
-        if (dn > a.nmax - n_prev) dn = a.nmax - n_prev;
-        const double *qs = a.qpow + (size_t)(dn - 1) * 32;
-        double w[4], w2[4];
+    int dn = 1 << (a.J - j);
+    if (dn > a.nmax - n_prev) dn = a.nmax - n_prev;
+    const double *qs = a.qpow + (size_t)(dn - 1) * 32;
+    double w = 0.0;
+    if (slot < a.R) {
+        w = 1.0;
+        uint32_t dd = (uint32_t)(a.E[slot] - a.emin[a.k]);
+        while (dd) {
+            w = __dmul_rn(w, __ldg(&qs[__ffs(dd) - 1]));
+            dd &= dd - 1u;
+        }
+    }
+    double s = w, s2 = __dmul_rn(w, w);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            double acc = 0.0;
-            if (valid[q]) {
-                acc = 1.0;
-                uint32_t dd = d[q];
-                while (dd) {
-                    const int b = __ffs(dd) - 1;
-                    acc = __dmul_rn(acc, __ldg(&qs[b]));
-                    dd &= dd - 1u;
-                }
-            }
-            w[q] = acc;
-            w2[q] = __dmul_rn(acc, acc);
-        }
-        double s = __dadd_rn(__dadd_rn(w[0], w[1]), __dadd_rn(w[2], w[3]));
-        double s2 = __dadd_rn(__dadd_rn(w2[0], w2[1]), __dadd_rn(w2[2], w2[3]));
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            s = __dadd_rn(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
-            s2 = __dadd_rn(s2, __shfl_xor_sync(0xFFFFFFFFu, s2, off));
-        }
-        if (lane == 0) {
-            sw[0][warp] = s;
-            sw[1][warp] = s2;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double A = sw[0][0], B = sw[1][0];
-            for (int w3 = 1; w3 < RS_THREADS / 32; ++w3) {
-                A = __dadd_rn(A, sw[0][w3]);
-                B = __dadd_rn(B, sw[1][w3]);
-            }
-            a.part[((size_t)j * 2 + 0) * a.nch + blockIdx.x] = A;
-            a.part[((size_t)j * 2 + 1) * a.nch + blockIdx.x] = B;
-        }
-        __syncthreads();
+    for (int off = 1; off < 32; off <<= 1) {
+        s = __dadd_rn(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
+        s2 = __dadd_rn(s2, __shfl_xor_sync(0xFFFFFFFFu, s2, off));
+    }
+    if (lane == 0) {
+        sw[0][warp] = s;
+        sw[1][warp] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double *v = sw[threadIdx.x];
+        for (int h = 1; h < RS_CHUNK / 32; h <<= 1)
+            for (int i = 0; i < RS_CHUNK / 32; i += 2 * h) v[i] = __dadd_rn(v[i], v[i + h]);
+        a.part[((size_t)j * 2 + threadIdx.x) * a.nch + blockIdx.x] = v[0];
     }
 }
 
@@ -493,15 +476,20 @@ __device__ double tree_sum_seq(const double *v, int n) {
     return st[0];
 }
 
+// Level choice. Mode 1: one warp per level j sums the chunk partials of w and
+// w*w in the tree's order (each lane a contiguous power-of-two block of
+// chunks, then butterflies; zero padding adds exact zeros), ESS_j = A^2 / B,
+// and the smallest j with ESS_j >= rho R is taken (else J).
 __global__ void k_ad_choose(AdaptArgs a) {
     const int n_prev = a.state[0];
-    const int lane = threadIdx.x;
+    const int lane = threadIdx.x & 31, lvl = threadIdx.x >> 5;
+    __shared__ int ok_lvl[32];
     if (n_prev >= a.nmax) {
-        if (lane == 0) a.active[a.k] = 0;
+        if (threadIdx.x == 0) a.active[a.k] = 0;
         return;
     }
     if (a.mode == 2) {
-        if (lane == 0) {
+        if (threadIdx.x == 0) {
             int j = a.state[1];
             if (a.k > 0) {
                 const double acc = (double)a.accepts[a.k - 1];
@@ -521,16 +509,28 @@ __global__ void k_ad_choose(AdaptArgs a) {
         }
         return;
     }
-    bool ok = false;
-    if (lane <= a.J) {
-        const double A = tree_sum_seq(a.part + ((size_t)lane * 2 + 0) * a.nch, a.nch);
-        const double B = tree_sum_seq(a.part + ((size_t)lane * 2 + 1) * a.nch, a.nch);
-        const double ess = __ddiv_rn(__dmul_rn(A, A), B);
-        ok = ess >= a.rhoR;
+    if (lvl <= a.J) {
+        int L = 1;
+        while (L < a.nch) L <<= 1;
+        const int blk = L > 32 ? L / 32 : 1;
+        const int lo = lane * blk, cnt = max(0, min(blk, a.nch - lo));
+        double A = tree_sum_seq(a.part + ((size_t)lvl * 2 + 0) * a.nch + min(lo, a.nch), cnt);
+        double B = tree_sum_seq(a.part + ((size_t)lvl * 2 + 1) * a.nch + min(lo, a.nch), cnt);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            A = __dadd_rn(A, __shfl_xor_sync(0xFFFFFFFFu, A, off));
+            B = __dadd_rn(B, __shfl_xor_sync(0xFFFFFFFFu, B, off));
+        }
+        if (lane == 0) ok_lvl[lvl] = __ddiv_rn(__dmul_rn(A, A), B) >= a.rhoR;
     }
-    const unsigned bal = __ballot_sync(0xFFFFFFFFu, ok);
-    if (lane == 0) {
-        const int j = bal ? __ffs(bal) - 1 : a.J;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int j = a.J;
+        for (int l = 0; l < a.J; ++l)
+            if (ok_lvl[l]) {
+                j = l;
+                break;
+            }
         int dn = 1 << (a.J - j);
         if (dn > a.nmax - n_prev) dn = a.nmax - n_prev;
         const int nk = n_prev + dn;
@@ -641,8 +641,8 @@ cudaError_t launch_nonlocal(const NlmArgs &a, void *scratch, cudaStream_t st, in
 }
 
 cudaError_t launch_adapt(const AdaptArgs &a, cudaStream_t st) {
-    if (a.mode != 2) k_ad_partials<<<a.nch, RS_THREADS, 0, st>>>(a);
-    k_ad_choose<<<1, 32, 0, st>>>(a);
+    if (a.mode != 2) k_ad_partials<<<dim3(a.nch, a.J + 1), RS_CHUNK, 0, st>>>(a);
+    k_ad_choose<<<1, a.mode == 2 ? 32 : 32 * (a.J + 1), 0, st>>>(a);
     return cudaGetLastError();
 }
 

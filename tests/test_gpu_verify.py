@@ -89,3 +89,31 @@ def test_cli_checkpoint_resume_and_curve(tmp_path):
     assert np.array_equal(c_full[:, [0, 1, 3]], c_res[:, [0, 1, 3]])
     assert np.all(np.diff(c_full[:, 3]) >= 0) and c_full[-1, 3] == full["best_cut"]
     assert np.all(np.diff(c_full[:, 2]) >= 0)
+
+
+def test_cli_adaptive_modes_equal_the_api(tmp_path):
+    """The CLI's adaptive-control options (ESS-adaptive steps, acceptance-rate
+    steps, stagnation reheating) run the same anneal as the Python API with
+    the same options: same steps, best cut and where it was found."""
+    require_gpu()
+    g = wl.gnm(500, 3000, seed=41)
+    gp = tmp_path / "g.txt"
+    wl.write_gset(g, str(gp))
+    common = ["--graph", gp, "--replicas", 256, "--sweeps", 2, "--beta", 0.1, 2.0, 60, "--variant", 2,
+              "--nlm-period", 0]
+    cases = [
+        (["--adaptive", 1, "--rho", 0.6, "--adapt-J", 6, "--dbeta-max", 0.2],
+         dict(adaptive=1, rho=0.6, adapt_J=6, adapt_dbeta_max=0.2, beta_max=2.0, acc_lo=0.05, acc_hi=0.25)),
+        (["--adaptive", 2, "--adapt-J", 5, "--dbeta-max", 0.3, "--acc-lo", 0.1, "--acc-hi", 0.3],
+         dict(adaptive=2, rho=0.5, adapt_J=5, adapt_dbeta_max=0.3, beta_max=2.0, acc_lo=0.1, acc_hi=0.3)),
+        (["--reheat-after", 3, "--reheat-back", 5], dict(reheat_after=3, reheat_back=5)),
+    ]
+    betas = wl.linear_betas(0.1, 2.0, 60)
+    for args, kw in cases:
+        out = _cli(*common, *args)
+        with B.Annealer.from_graph(g) as a:
+            a.anneal(None if kw.get("adaptive") else betas, 256, 2, 0, K=60, nlm_period=0, **kw)
+            st = a.stats()
+            E, step, sweep, slot = a.best_record()
+        assert out["steps"] == st["steps_run"]
+        assert out["best_cut"] == (st["total_weight"] - E) // 2 and out["best_step"] == step, args
