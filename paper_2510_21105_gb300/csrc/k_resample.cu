@@ -78,53 +78,43 @@ __global__ void k_fields_energy(GraphDev g, const int8_t *spins, int16_t *fields
     }
 }
 
-__global__ void k_rs_min(ResampleArgs a) {
+// The resampling kernels run one CTA of RS_CHUNK threads per chunk of
+// RS_CHUNK slots, one slot per thread.
+__global__ void __launch_bounds__(RS_CHUNK) k_rs_min(ResampleArgs a) {
     if (a.active && !a.active[a.k]) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.stamp[a.k] = gtimer();
-    const int base = blockIdx.x * RS_CHUNK + threadIdx.x * 4;
-    int v = 0x7FFFFFFF;
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-        if (base + q < a.R) v = min(v, a.E[base + q]);
+    const int r = blockIdx.x * RS_CHUNK + threadIdx.x;
+    int v = r < a.R ? a.E[r] : 0x7FFFFFFF;
     v = __reduce_min_sync(0xFFFFFFFFu, v);
     if ((threadIdx.x & 31) == 0) atomicMin(&a.emin[a.k], v);
 }
 
-__global__ void k_rs_weights(ResampleArgs a) {
+__global__ void __launch_bounds__(RS_CHUNK) k_rs_weights(ResampleArgs a) {
     if (a.active && !a.active[a.k]) return;
     __shared__ double qs[32];
-    __shared__ double wsum[RS_THREADS / 32];
-    __shared__ unsigned long long tsum[RS_THREADS / 32];
+    __shared__ double wsum[RS_CHUNK / 32];
+    __shared__ unsigned long long tsum[RS_CHUNK / 32];
     const int row = a.qsel ? a.qsel[a.k] : a.k;
     if (threadIdx.x < 32) qs[threadIdx.x] = a.qpow[(size_t)row * 32 + threadIdx.x];
     __syncthreads();
-    const int emin = a.emin[a.k];
-    const int base = blockIdx.x * RS_CHUNK + threadIdx.x * 4;
-    double w[4];
-    unsigned long long t[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        w[q] = 0.0;
-        t[q] = 0ull;
-        if (base + q < a.R) {
-            uint32_t d = (uint32_t)(a.E[base + q] - emin);
-            double acc = 1.0;
-            while (d) {
-                const int b = __ffs(d) - 1;
-                acc = __dmul_rn(acc, qs[b]);
-                d &= d - 1u;
-            }
-            w[q] = acc;
-            t[q] = (unsigned long long)__dmul_rn(acc, 4294967296.0);
+    const int r = blockIdx.x * RS_CHUNK + threadIdx.x;
+    double w = 0.0;
+    unsigned long long t = 0ull;
+    if (r < a.R) {
+        uint32_t d = (uint32_t)(a.E[r] - a.emin[a.k]);
+        w = 1.0;
+        while (d) {
+            w = __dmul_rn(w, qs[__ffs(d) - 1]);
+            d &= d - 1u;
         }
+        t = (unsigned long long)__dmul_rn(w, 4294967296.0);
     }
-    // Pairwise tree: (w0 + w1) + (w2 + w3), then lane butterflies, then warps.
-    double s = __dadd_rn(__dadd_rn(w[0], w[1]), __dadd_rn(w[2], w[3]));
+    // Pairwise tree: lane butterflies (32 slots), then the eight warp sums in pairs.
+    double s = w;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) s = __dadd_rn(s, __shfl_xor_sync(0xFFFFFFFFu, s, off));
     // Exclusive prefix of t over the chunk.
-    unsigned long long tt = t[0] + t[1] + t[2] + t[3];
-    unsigned long long inc = tt;
+    unsigned long long inc = t;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
@@ -136,39 +126,46 @@ __global__ void k_rs_weights(ResampleArgs a) {
         tsum[warp] = inc;
     }
     __syncthreads();
-    unsigned long long pre = inc - tt;
+    unsigned long long pre = inc - t;
     for (int w2 = 0; w2 < warp; ++w2) pre += tsum[w2];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        a.ploc[base + q] = pre;     // sized nch * RS_CHUNK; slots past R hold t = 0
-        a.tval[base + q] = t[q];
-        pre += t[q];
-    }
+    a.ploc[r] = pre;   // sized nch * RS_CHUNK; slots past R hold t = 0
+    a.tval[r] = t;
     if (threadIdx.x == 0) {
-        double c = wsum[0];
-        for (int w2 = 1; w2 < RS_THREADS / 32; ++w2) c = __dadd_rn(c, wsum[w2]);   // two warps: one level
+        for (int h = 1; h < RS_CHUNK / 32; h <<= 1)
+            for (int i = 0; i < RS_CHUNK / 32; i += 2 * h) wsum[i] = __dadd_rn(wsum[i], wsum[i + h]);
         unsigned long long ct = 0;
-        for (int w2 = 0; w2 < RS_THREADS / 32; ++w2) ct += tsum[w2];
-        a.partA[blockIdx.x] = c;
+        for (int w2 = 0; w2 < RS_CHUNK / 32; ++w2) ct += tsum[w2];
+        a.partA[blockIdx.x] = wsum[0];
         a.partT[blockIdx.x] = ct;
     }
 }
 
-// floor((P R 2^32 + o T) / (T 2^32)) for R <= 65536; written as
-// floor(P R / T) + [ (P R mod T) 2^32 >= T (2^32 - o) ].
-__device__ __forceinline__ int32_t systematic_count(unsigned long long P, int32_t R,
-                                                    unsigned long long T, uint32_t o) {
+// floor((P R 2^32 + o T) / (T 2^32)) for R <= 65536, written as
+// floor(P R / T) + [ (P R mod T) 2^32 >= T (2^32 - o) ]. The division by T
+// goes through m = floor((2^64 - 1) / T), computed once per step: q =
+// mulhi(X, m) satisfies X/T - 2 < q <= X/T (m >= (2^64 - T)/T and X < 2^64),
+// so at most two corrections make it exact.
+__device__ __forceinline__ int32_t systematic_count_m(unsigned long long P, int32_t R, unsigned long long T,
+                                                      unsigned long long m, uint32_t o) {
     if (P >= T) return R;
     const unsigned long long X = P * (unsigned long long)R;
-    const unsigned long long q = X / T, r = X - q * T;
+    unsigned long long q = __umul64hi(X, m), r = X - q * T;
+    if (r >= T) {
+        ++q;
+        r -= T;
+    }
+    if (r >= T) {
+        ++q;
+        r -= T;
+    }
     const unsigned __int128 lhs = (unsigned __int128)r << 32;
     const unsigned __int128 rhs = (unsigned __int128)T * (0x100000000ull - (unsigned long long)o);
     return (int32_t)(q + (lhs >= rhs ? 1ull : 0ull));
 }
 
-__global__ void k_rs_parents(ResampleArgs a) {
+__global__ void __launch_bounds__(RS_CHUNK) k_rs_parents(ResampleArgs a) {
     if (a.active && !a.active[a.k]) return;
-    __shared__ unsigned long long sh_T, sh_off;
+    __shared__ unsigned long long sh_T, sh_off, sh_m;
     __shared__ uint32_t sh_o;
     if (threadIdx.x < 32) {   // warp 0: totals over the chunks
         const int lane = threadIdx.x;
@@ -211,6 +208,7 @@ __global__ void k_rs_parents(ResampleArgs a) {
         }
         if (lane == 0) {
             sh_T = T;
+            sh_m = T ? ~0ull / T : 0ull;
             sh_off = off;
             sh_o = philox10(make_uint4(0u, 0u, (uint32_t)a.k, TAG_RESAMPLE), a.key0, a.key1).x;
             if (blockIdx.x == 0) {
@@ -221,19 +219,18 @@ __global__ void k_rs_parents(ResampleArgs a) {
         }
     }
     __syncthreads();
-    const unsigned long long T = sh_T, off = sh_off;
+    const unsigned long long T = sh_T, off = sh_off, m = sh_m;
     const uint32_t o = sh_o;
-    const int base = blockIdx.x * RS_CHUNK + threadIdx.x * 4;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int r = base + q;
-        if (r < a.R) {
-            const unsigned long long P = off + a.ploc[r];
-            const int32_t lo = systematic_count(P, a.R, T, o);
-            const int32_t hi = systematic_count(P + a.tval[r], a.R, T, o);
-            for (int s = lo; s < hi; ++s) a.parent[s] = r;
-            if (a.counts) a.counts[(size_t)a.k * a.R + r] = hi - lo;
-        }
+    const int r = blockIdx.x * RS_CHUNK + threadIdx.x;
+    // Slot r fills new slots [F(P_r), F(P_r + t_r)); P_r + t_r = P_{r+1} inside
+    // the chunk, so the upper end is the next lane's lower end.
+    const unsigned long long P = off + a.ploc[r];
+    const int32_t lo = systematic_count_m(P, a.R, T, m, o);
+    int32_t hi = __shfl_down_sync(0xFFFFFFFFu, lo, 1);
+    if ((threadIdx.x & 31) == 31) hi = systematic_count_m(P + a.tval[r], a.R, T, m, o);
+    if (r < a.R) {
+        for (int s = lo; s < hi; ++s) a.parent[s] = r;
+        if (a.counts) a.counts[(size_t)a.k * a.R + r] = hi - lo;
     }
 }
 
@@ -257,13 +254,13 @@ cudaError_t launch_fields(const GraphDev &g, const int8_t *spins, int16_t *field
 }
 
 cudaError_t launch_rs_min(const ResampleArgs &a, cudaStream_t st) {
-    k_rs_min<<<a.nch, RS_THREADS, 0, st>>>(a);
+    k_rs_min<<<a.nch, RS_CHUNK, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_rs_rest(const ResampleArgs &a, cudaStream_t st) {
-    k_rs_weights<<<a.nch, RS_THREADS, 0, st>>>(a);
-    k_rs_parents<<<a.nch, RS_THREADS, 0, st>>>(a);
+    k_rs_weights<<<a.nch, RS_CHUNK, 0, st>>>(a);
+    k_rs_parents<<<a.nch, RS_CHUNK, 0, st>>>(a);
     return cudaGetLastError();
 }
 

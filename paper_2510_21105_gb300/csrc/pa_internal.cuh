@@ -79,7 +79,6 @@ static __device__ __forceinline__ bool accept_by_top_byte(uint32_t top, uint32_t
 
 constexpr int32_t EMIN_SENTINEL = 0x7F7F7F7F;  // byte-fillable "+infinity"
 constexpr int RS_CHUNK = 256;                   // slots per resampling CTA (power of two)
-constexpr int RS_THREADS = 64;                  // 4 slots per thread
 
 struct GraphDev {
     int32_t n, np, ncol, mmax;
