@@ -1,6 +1,7 @@
 // k_moves.cu -- Houdayer non-local moves and ESS-adaptive temperature steps
 // (Sec. 3 of arXiv 2510.21105 names both without defining them; the rules
 // implemented here are the library's readings, stated in pa_moves.cuh).
+#include <algorithm>
 #include <mutex>
 
 #include "pa_moves.cuh"
@@ -9,34 +10,90 @@ namespace pa {
 namespace {
 
 // ------------------------------------------------------------ non-local ---
-__global__ void k_nlm_keys(NlmArgs a, uint32_t *keys) {
+// Pairing: slots sorted by (key_r, r), consecutive entries paired. The rank of
+// (key_r, r) is found through NB = 2^b buckets of the top b key bits (about
+// 32 slots each for uniform keys): bucket counts, their exclusive scan, the
+// slots listed bucket by bucket, then each slot counts the smaller pairs of
+// its own bucket. Any key distribution gives the exact rank.
+struct NlmRankScratch {
+    uint32_t *keys;     // [R]
+    int32_t *order;     // [R] slot of each rank
+    int32_t *members;   // [R] slots grouped by bucket
+    int32_t *start;     // [NB + 1] bucket counts, then their exclusive scan
+    int32_t *fill;      // [NB]
+    int32_t NB, shift;  // bucket = NB > 1 ? key >> shift : 0
+};
+
+__host__ __device__ inline int nlm_buckets(int32_t R) {
+    int nb = 1;
+    while (nb < 2048 && 32 * nb < R) nb <<= 1;
+    return nb;
+}
+
+__device__ __forceinline__ int nlm_bucket(uint32_t key, const NlmRankScratch &s) {
+    return s.NB > 1 ? (int)(key >> s.shift) : 0;
+}
+
+__global__ void k_nlm_keys(NlmArgs a, NlmRankScratch s) {
+    if (a.active && !a.active[a.k]) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r <= s.NB) s.start[r] = 0;
+    if (r < s.NB) s.fill[r] = 0;
+    if (r >= a.R) return;
+    const uint4 u = philox10(make_uint4((uint32_t)r >> 2, 0u, (uint32_t)a.k, TAG_NONLOCAL), a.key0, a.key1);
+    s.keys[r] = (r & 3) == 0 ? u.x : (r & 3) == 1 ? u.y : (r & 3) == 2 ? u.z : u.w;
+}
+
+__global__ void k_nlm_count(NlmArgs a, NlmRankScratch s) {
+    if (a.active && !a.active[a.k]) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < a.R) atomicAdd(&s.start[nlm_bucket(s.keys[r], s)], 1);
+}
+
+// Exclusive scan of the NB <= 2048 bucket counts, one CTA of 1024 threads.
+__global__ void __launch_bounds__(1024) k_nlm_scan(NlmArgs a, NlmRankScratch s) {
+    if (a.active && !a.active[a.k]) return;
+    __shared__ int wsum[32];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int c0 = 2 * t < s.NB ? s.start[2 * t] : 0, c1 = 2 * t + 1 < s.NB ? s.start[2 * t + 1] : 0;
+    int inc = c0 + c1;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, inc, off);
+        if (lane >= off) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    int pre = inc - c0 - c1;
+    for (int w = 0; w < warp; ++w) pre += wsum[w];
+    __syncthreads();   // every count is read before the starts overwrite them
+    if (2 * t < s.NB) s.start[2 * t] = pre;
+    if (2 * t + 1 < s.NB) s.start[2 * t + 1] = pre + c0;
+    if (t == 0) s.start[s.NB] = a.R;
+}
+
+__global__ void k_nlm_fill(NlmArgs a, NlmRankScratch s) {
     if (a.active && !a.active[a.k]) return;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.R) return;
-    const uint4 u = philox10(make_uint4((uint32_t)r >> 2, 0u, (uint32_t)a.k, TAG_NONLOCAL), a.key0, a.key1);
-    const uint32_t uu[4] = {u.x, u.y, u.z, u.w};
-    keys[r] = uu[r & 3];
+    const int b = nlm_bucket(s.keys[r], s);
+    s.members[s.start[b] + atomicAdd(&s.fill[b], 1)] = r;
 }
 
-// Rank of (key_r, r) among all slots by direct counting; order[rank] = r.
-__global__ void k_nlm_rank(NlmArgs a, const uint32_t *keys, int32_t *order) {
+__global__ void k_nlm_rank(NlmArgs a, NlmRankScratch s) {
     if (a.active && !a.active[a.k]) return;
-    __shared__ uint32_t tile[2048];
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t kr = r < a.R ? keys[r] : 0u;
-    int rank = 0;
-    for (int t0 = 0; t0 < a.R; t0 += 2048) {
-        const int tn = min(2048, a.R - t0);
-        __syncthreads();
-        for (int i = threadIdx.x; i < tn; i += blockDim.x) tile[i] = keys[t0 + i];
-        __syncthreads();
-        if (r < a.R)
-            for (int i = 0; i < tn; ++i) {
-                const uint32_t ks = tile[i];
-                rank += (ks < kr) || (ks == kr && t0 + i < r);
-            }
+    if (r >= a.R) return;
+    const uint32_t kr = s.keys[r];
+    const int b = nlm_bucket(kr, s);
+    const int lo = s.start[b], hi = s.start[b + 1];
+    int rank = lo;
+    for (int i = lo; i < hi; ++i) {
+        const int m = s.members[i];
+        const uint32_t km = s.keys[m];
+        rank += (km < kr) || (km == kr && m < r);
     }
-    if (r < a.R) order[rank] = r;
+    s.order[rank] = r;
 }
 
 // Spin bits of 32 positions (32 bytes of a row, +1 -> 1; -1 and padding -> 0).
@@ -585,7 +642,9 @@ cudaError_t launch_reheat(const ReheatArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-size_t nlm_scratch_bytes(int32_t R) { return (size_t)R * 8 + 256; }
+size_t nlm_scratch_bytes(int32_t R) {   // keys, order, members, bucket starts and fills
+    return (size_t)R * 12 + (size_t)(2 * nlm_buckets(R) + 1) * 4 + 256;
+}
 
 size_t nlm_smem_bytes(int32_t np) {   // spin bitsets of both replicas, candidates, queue
     return 3 * 4 * (size_t)((np + 31) / 32) + 2 * (size_t)np + 16;
@@ -616,12 +675,24 @@ cudaError_t launch_nonlocal(const NlmArgs &a, void *scratch, cudaStream_t st, in
         *launches = 1;
         return cudaGetLastError();
     }
-    uint32_t *keys = reinterpret_cast<uint32_t *>(scratch);
-    int32_t *order = reinterpret_cast<int32_t *>(keys + a.R);
+    NlmRankScratch rs;
+    rs.keys = reinterpret_cast<uint32_t *>(scratch);
+    rs.order = reinterpret_cast<int32_t *>(rs.keys + a.R);
+    rs.members = rs.order + a.R;
+    rs.NB = nlm_buckets(a.R);
+    rs.start = rs.members + a.R;
+    rs.fill = rs.start + rs.NB + 1;
+    int lg = 0;
+    while ((1 << lg) < rs.NB) ++lg;
+    rs.shift = 32 - lg;
     const int nb = (a.R + 255) / 256;
-    k_nlm_keys<<<nb, 256, 0, st>>>(a, keys);
-    k_nlm_rank<<<nb, 256, 0, st>>>(a, keys, order);
-    *launches = 2;
+    k_nlm_keys<<<(std::max(a.R, rs.NB + 1) + 255) / 256, 256, 0, st>>>(a, rs);
+    k_nlm_count<<<nb, 256, 0, st>>>(a, rs);
+    k_nlm_scan<<<1, 1024, 0, st>>>(a, rs);
+    k_nlm_fill<<<nb, 256, 0, st>>>(a, rs);
+    k_nlm_rank<<<nb, 256, 0, st>>>(a, rs);
+    const int32_t *order = rs.order;
+    *launches = 5;
     if (a.R >= 2) {
         const size_t smem = nlm_smem_bytes(a.g.np);
         static std::mutex mu;
@@ -635,7 +706,7 @@ cudaError_t launch_nonlocal(const NlmArgs &a, void *scratch, cudaStream_t st, in
             }
         }
         k_nlm_pair<<<a.R / 2, 256, smem, st>>>(a, order);
-        *launches = 3;
+        *launches = 6;
     }
     return cudaGetLastError();
 }
