@@ -97,6 +97,19 @@ def test_parity_nonlocal_moves(variant):
     assert_parity(gpu, orc, g, 64, 3)
 
 
+@pytest.mark.parametrize("R", [2, 8, 32, 33, 65])
+def test_parity_nonlocal_moves_small_populations(R):
+    """Houdayer pairing through key buckets at the smallest populations: one
+    bucket (R <= 32), two and four buckets, and an odd R whose last slot stays
+    unpaired."""
+    g = wl.gnm(200, 800, seed=R)
+    betas = wl.linear_betas(0.1, 2.5, 8)
+    gpu = run_gpu(g, betas, R, 2, seed=5 + R, nlm_period=2)
+    orc = run_oracle(g, betas, R, 2, seed=5 + R, nlm_period=2)
+    assert orc.step_nlm_pairs.sum() > 0
+    assert_parity(gpu, orc, g, R, 2)
+
+
 @pytest.mark.parametrize("variant", [0, 1, 3])
 @pytest.mark.parametrize("n,m", [(600, 900), (300, 3000)])
 def test_parity_nonlocal_moves_low_and_high_degree(variant, n, m):
