@@ -329,6 +329,18 @@ def test_parity_msc_many_words_ragged_last_word(variant, extra):
     assert_parity(gpu, orc, g, 4937, 2)
 
 
+@pytest.mark.parametrize("variant", [1, 3])
+def test_parity_msc_above_padded_rows(variant):
+    """n = 17000 (> 16384 positions, beyond the 16-bit padded rows): the
+    multi-spin-coded kernels read the plain CSR, with a single-bond tail per
+    row; signed weights, mean degree 12, max degree above 15."""
+    g = wl.from_edges(17000, *_random_edges(17000, 102000, seed=5))
+    betas = wl.linear_betas(0.1, 2.5, 4)
+    gpu = run_gpu(g, betas, 64, 2, seed=21, variant=variant)
+    orc = run_oracle(g, betas, 64, 2, seed=21)
+    assert_parity(gpu, orc, g, 64, 2)
+
+
 def test_parity_largest_graph_that_fits_shared_memory():
     """n = 40000: too large for the packed (n <= 32720) and int16 layouts, so
     AUTO falls back to multi-spin coding even with fewer words than SMs; block
