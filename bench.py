@@ -231,7 +231,7 @@ def run_reference(args, rank, world):
 # tail launches of the multi-spin-coded sweep, or the one launch of another
 # layout), from one ncu capture, with the SHA-256 prefix of the sweep source it
 # was taken on: reported only while that source is the one that runs.
-SWEEP_TRAFFIC = {"k_sweep_msc+pair": ((102.907904 + 44.890112 + 12.868608) * 1e6, "7c93717a46171f76")}
+SWEEP_TRAFFIC = {"k_sweep_msc+pair": ((102.875648 + 44.824064 + 12.869376) * 1e6, "6ca9288e529d8511")}
 SWEEP_SRC = os.path.join(ROOT, "paper_2510_21105_gb300", "csrc", "k_sweep.cu")
 INT_LANES_PER_SM = 128   # ALU pipe 64 + FMA pipe 64 integer lanes per SM and clock (unit counts)
 SMEM_BYTES_PER_SM = 128  # shared-memory bytes per SM and clock (32 banks x 4 B)

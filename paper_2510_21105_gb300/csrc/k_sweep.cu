@@ -822,6 +822,23 @@ __device__ __forceinline__ void msc_step4x(uint32_t (&A)[NPL], uint32_t x, uint3
     }
 }
 
+// Delta swap of the bits selected by M between x >> s and y; zx, zy say that
+// x or y is known to be zero (then the swap is a mask and a shift).
+__device__ __forceinline__ void msc_swap(uint32_t &x, uint32_t &y, int s, uint32_t M, bool zx, bool zy) {
+    if (zx && zy) return;
+    if (zy) {
+        y = (x >> s) & M;
+        x &= ~(M << s);
+    } else if (zx) {
+        x = (y & M) << s;
+        y &= ~M;
+    } else {
+        const uint32_t t = ((x >> s) ^ y) & M;
+        x ^= t << s;
+        y ^= t;
+    }
+}
+
 template <int NPL, bool WEIGHTED>
 __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t *Wsm, const uint32_t *T256, int p,
                                              uint32_t x, uint32_t c3, int blk, int32_t *Eacc,
@@ -891,27 +908,20 @@ __device__ __forceinline__ uint32_t msc_item(const SweepArgs &a, const uint32_t 
     philox_from_shared2(philox_shared(vid, (uint32_t)a.k, c3, a.key0, a.key1), 2u * blk, 2u * blk + 1u, a.rk0, a.rk1,
                         u0, u1);
     // Byte q of r[g] = c of replica 4g + q: an 8 x 8 bit transpose in every byte lane.
+    // Planes NPL..7 are zero, so a swap with a known-zero partner is a mask and
+    // a shift (msc_swap); the zero set after each stage follows from NPL alone.
     uint32_t r[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) r[b] = b < NPL ? pl[b] : 0u;
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const uint32_t t = ((r[b] >> 4) ^ r[b + 4]) & 0x0F0F0F0Fu;
-        r[b] ^= t << 4;
-        r[b + 4] ^= t;
-    }
+    for (int b = 0; b < 4; ++b) msc_swap(r[b], r[b + 4], 4, 0x0F0F0F0Fu, b >= NPL, b + 4 >= NPL);
 #pragma unroll
-    for (int b = 0; b < 8; b += (b & 1) ? 3 : 1) {   // 0, 1, 4, 5
-        const uint32_t t = ((r[b] >> 2) ^ r[b + 2]) & 0x33333333u;
-        r[b] ^= t << 2;
-        r[b + 2] ^= t;
-    }
+    for (int b = 0; b < 8; b += (b & 1) ? 3 : 1)   // 0, 1, 4, 5
+        msc_swap(r[b], r[b + 2], 2, 0x33333333u, (b & 3) >= NPL, ((b + 2) & 3) >= NPL);
 #pragma unroll
-    for (int b = 0; b < 8; b += 2) {
-        const uint32_t t = ((r[b] >> 1) ^ r[b + 1]) & 0x55555555u;
-        r[b] ^= t << 1;
-        r[b + 1] ^= t;
-    }
+    for (int b = 0; b < 8; b += 2)
+        msc_swap(r[b], r[b + 1], 1, 0x55555555u, (b & 3) >= NPL && ((b ^ 2) & 3) >= NPL,
+                 ((b + 1) & 3) >= NPL && (((b + 1) ^ 2) & 3) >= NPL);
     uint32_t acc32 = 0, acct32 = 0;   // accepted; accepted or tied
     const uint32_t mq0 = (32u - deg) * 0x01010101u;   // 2c + 32 - deg = m + 32 per byte (PK)
     const unsigned char *tb = reinterpret_cast<const unsigned char *>(T256);
