@@ -606,9 +606,11 @@ def _serve_trace(seconds, rate, seed=1):
 
 
 def _serve(trace, betas, slots, saturated, steps_per_tick=8):
-    """saturated: other requests keep the GPU full, so each request uses the
-    kernel with the cheapest attempt (multi-spin coded, every word in one-CTA
-    blocks); otherwise each uses the automatic choice for a GPU of its own."""
+    """Every request asks for the automatic layout. The server gives a request
+    admitted while others run the cheapest attempt on a shared device
+    (multi-spin coded, every word in one-CTA blocks) and one admitted alone the
+    single-instance choice; with one slot (the plain arm) every request runs
+    alone. saturated only labels the arm."""
     from paper_2510_21105_gb300 import binding as B
 
     with B.Server(200 << 30, n_streams=slots, steps_per_tick=steps_per_tick) as srv:
@@ -618,8 +620,7 @@ def _serve(trace, betas, slots, saturated, steps_per_tick=8):
             delay = at - (time.perf_counter() - t0)
             if delay > 0:
                 time.sleep(delay)
-            sat = saturated and g.maxdeg <= 127
-            ids.append(srv.submit(g, betas, R, 4, seed, variant=1 if sat else 2, msc_no_split=int(sat)))
+            ids.append(srv.submit(g, betas, R, 4, seed, variant=2))
         res = {}
         while len(res) < len(ids):
             for rid in ids:

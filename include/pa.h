@@ -304,9 +304,12 @@ int pa_batch_anneal(const pa_job *jobs, int32_t n_jobs, const pa_batch_opts *opt
  * their populations resident, and advances every admitted request, each on
  * its own stream, by steps_per_tick temperature steps per tick, so requests
  * that arrive while others run overlap with them on the device (continuous
- * batching). Each result is bit-identical to
- * the same request run alone with pa_anneal. Times are host milliseconds
- * since pa_server_start.
+ * batching). A request with opts.variant = PA_VARIANT_AUTO that is admitted
+ * while other requests run takes the multi-spin-coded layout with every word
+ * in one-CTA blocks (msc_no_split = 1: the cheapest attempt on a shared
+ * device; max degree <= 127); admitted alone it keeps the automatic choice.
+ * Each result is bit-identical to the same request run alone with pa_anneal.
+ * Times are host milliseconds since pa_server_start.
  */
 typedef struct pa_server pa_server;
 

@@ -102,7 +102,7 @@ size_t estimate_bytes(const Request &q) {
     b += (rpad / 4) * (np + 16);                    // best records and configurations
     b += K * (size_t)(maxdeg + 1) * 4 + K * 32 * 8 + K * (64 + 4 * (size_t)std::max(q.S, 1));
     b += m2 * 6 + np * 24;                          // graph copies
-    if (q.opts.nlm_period > 0) b += (size_t)q.R * 8;
+    if (q.opts.nlm_period > 0) b += (size_t)q.R * 12 + 16384;
     return b + (1u << 20);
 }
 
@@ -156,6 +156,21 @@ bool admit_one(pa_server *s, const std::shared_ptr<Request> &q) {
         pa_anneal_opts o = q->opts;
         o.stream = q->stream;
         o.time_kernels = 0;
+        // Layout by load: an automatic-layout request admitted while others run
+        // shares the device, so it takes the cheapest attempt (multi-spin coded,
+        // every word in one-CTA blocks); admitted alone it keeps the automatic
+        // single-instance choice. Results do not depend on the layout.
+        bool shared;
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            shared = !s->active.empty() || s->preparing > 1;
+        }
+        int32_t maxdeg = 0;
+        for (int32_t i = 0; i < q->n; ++i) maxdeg = std::max<int32_t>(maxdeg, (int32_t)(q->rp[i + 1] - q->rp[i]));
+        if (o.variant == PA_VARIANT_AUTO && shared && maxdeg <= 127) {
+            o.variant = PA_VARIANT_MSC;
+            o.msc_no_split = 1;
+        }
         rc = pa_anneal_begin(q->ctx, q->betas.empty() ? nullptr : q->betas.data(), q->K, q->R, q->S, q->seed, &o);
     }
     if (rc != PA_OK) {
