@@ -324,7 +324,11 @@ def sweep_roofline(stats, attempts_per_launch, probe, clk_mhz, kernel, mean_degr
             "smem_bytes_per_attempt": sbpa, "smem_frac": aps * sbpa / smem_peak,
             "smem_frac_vs_derived": aps * sbpa / smem_derived,
             "smem_target_met": aps * sbpa / smem_peak >= 0.5,
-            "philox_frac": (aps * (0.25 if msc else 1.0) / probe["philox_words_per_s"]) if probe else None}
+            "philox_frac": (aps * (0.25 if msc else 1.0) / probe["philox_words_per_s"]) if probe else None,
+            # The same rate against the count of the first formulation (plain carry-save adders, one table lookup
+            # per replica: (4.5 d + 288)/32), which stays fixed across builds and so tracks the kernel's progress.
+            "ops_per_attempt_first_formulation": (4.5 * mean_degree + 288.0) / 32.0 if msc else None,
+            "frac_first_formulation": aps * (4.5 * mean_degree + 288.0) / 32.0 / 1e12 / peak if msc else None}
 
 
 def max_over_ranks(x: float, dist, device: str = "cpu") -> float:

@@ -40,6 +40,7 @@ def test_sweep_roofline_fractions():
     assert r["avg_launch_ms"] == pytest.approx(1.5)
     assert r["attempts_per_s_in_kernel"] == pytest.approx(aps)
     assert r["achieved"] == pytest.approx(aps * bench.msc_ops_per_attempt(12.0) / 1e12)
+    assert r["frac_first_formulation"] == pytest.approx(aps * (4.5 * 12.0 + 288) / 32 / 1e12 / 30.0)
     assert r["peak"] == pytest.approx(30.0) and r["frac"] == pytest.approx(r["achieved"] / 30.0)
     assert r["peak_derived"] == pytest.approx(152 * 128 * 2000e6 / 1e12)
     assert r["smem_frac"] == pytest.approx(aps * (8 + 6 * 12.0) / 32 / 38e12)
