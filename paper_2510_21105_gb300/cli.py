@@ -2,7 +2,7 @@
 
     python -m paper_2510_21105_gb300.cli [--config g63like | --graph FILE]
         [--steps K] [--seed S] [--replicas R] [--sweeps S] [--beta LO HI K]
-        [--nlm-period P] [--nlm-kind 0|1] [--nlm-block B] [--variant 0|1|2] [--field-bits 16|8|7]
+        [--nlm-period P] [--nlm-kind 0|1] [--nlm-block B] [--variant 0|1|2|3] [--field-bits 16|8|7]
         [--replicas-per-cta 4|8] [--threads T] [--hex] [--save-hex FILE]
         [--curve FILE] [--checkpoint FILE --checkpoint-every K] [--resume FILE]
         [--adaptive 1|2 [--rho F] [--adapt-J J] [--dbeta-max D] [--beta-max B] [--acc-lo F --acc-hi F]]
@@ -94,7 +94,8 @@ def _anneal(argv):
     p.add_argument("--field-bits", type=int, default=0)
     p.add_argument("--replicas-per-cta", type=int, default=0)
     p.add_argument("--threads", type=int, default=0)
-    p.add_argument("--variant", type=int, default=0)
+    p.add_argument("--variant", type=int, default=2,
+                   help="0 int8/int16 fields, 1 multi-spin coded, 2 automatic (default), 3 CTA pairs")
     p.add_argument("--hex", action="store_true")
     p.add_argument("--save-hex", default=None)
     p.add_argument("--curve", default=None, help="write step,beta,t_ms,best_cut CSV")

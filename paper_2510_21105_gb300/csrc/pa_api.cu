@@ -100,6 +100,11 @@ struct RunState {
     // rest in the CTA-pair kernel on a second stream, concurrently, so every
     // SM carries the same share.
     bool split = false;
+    // Adaptive runs end on the device (the controller reaches beta_max); the
+    // host reads the active flag of a step behind the ones it enqueues, through
+    // pinned slots, and stops enqueueing no-op steps (pa_anneal_run).
+    int32_t *end_flag = nullptr;         // pinned [END_WINDOW]
+    cudaEvent_t end_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     pa::SweepConfig sweep2{};
     int32_t nblk2 = 0, blk_base2 = 0;
     cudaStream_t st2 = nullptr;
@@ -231,6 +236,15 @@ void free_run_events(RunState &r) {
     for (cudaEvent_t e : r.ev_sweep) cudaEventDestroy(e);
     r.ev_pending.clear();
     r.ev_sweep.clear();
+    for (cudaEvent_t &e : r.end_ev)
+        if (e) {
+            cudaEventDestroy(e);
+            e = nullptr;
+        }
+    if (r.end_flag) {
+        cudaFreeHost(r.end_flag);
+        r.end_flag = nullptr;
+    }
 }
 
 // Fold finished event pairs into the timing totals (call after a sync).
@@ -934,8 +948,42 @@ int pa_anneal_run(pa_ctx *c, int32_t k_end) {
     r.ev_pending.push_back(e0);
     r.ev_pending.push_back(e1);
     PA_CUDA(c, cudaEventRecord(e0, st));
-    for (int32_t k = r.k_done; k < k_end; ++k)
-        if (int rc = enqueue_step(c, k, st, r.opts.time_kernels != 0)) return rc;
+    // Adaptive runs: once the controller has reached beta_max every later step
+    // is a no-op on the device. Enqueue in chunks of END_CHUNK steps, copy the
+    // active flag of each chunk's last step to a pinned slot, and keep at most
+    // END_WINDOW chunks ahead of the last flag read; a flag of 0 ends the loop
+    // (the skipped steps count as done, exactly as if they had run). Not while
+    // the stream is being captured, where the host may not wait.
+    constexpr int32_t END_CHUNK = 32, END_WINDOW = 4;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cap);
+    bool poll = r.opts.adaptive != 0 && cap == cudaStreamCaptureStatusNone;
+    if (poll && !r.end_flag) {
+        if (cudaHostAlloc(reinterpret_cast<void **>(&r.end_flag), 4 * END_WINDOW, cudaHostAllocDefault) != cudaSuccess) {
+            r.end_flag = nullptr;
+            poll = false;
+        }
+        for (int i = 0; poll && i < END_WINDOW; ++i)
+            if (cudaEventCreateWithFlags(&r.end_ev[i], cudaEventDisableTiming) != cudaSuccess) poll = false;
+        cudaGetLastError();
+    }
+    poll = poll && r.end_flag && r.end_ev[END_WINDOW - 1];
+    int32_t chunk = 0;
+    bool ended = false;
+    for (int32_t k = r.k_done; k < k_end && !ended;) {
+        const int32_t kc = poll ? std::min(k_end, k + END_CHUNK) : k_end;
+        for (; k < kc; ++k)
+            if (int rc = enqueue_step(c, k, st, r.opts.time_kernels != 0)) return rc;
+        if (!poll || k >= k_end) break;
+        const int slot = chunk % END_WINDOW;
+        if (chunk >= END_WINDOW) {   // the slot's earlier copy: wait for it, then read it
+            PA_CUDA(c, cudaEventSynchronize(r.end_ev[slot]));
+            if (r.end_flag[slot] == 0) ended = true;
+        }
+        PA_CUDA(c, cudaMemcpyAsync(r.end_flag + slot, r.ad_active.as<int32_t>() + (k - 1), 4, cudaMemcpyDeviceToHost, st));
+        PA_CUDA(c, cudaEventRecord(r.end_ev[slot], st));
+        ++chunk;
+    }
     PA_CUDA(c, pa::launch_stamp(r.rec_stamp.as<unsigned long long>() + k_end, st));
     r.launches += 1;
     PA_CUDA(c, cudaEventRecord(e1, st));
