@@ -212,8 +212,13 @@ int pa_anneal_begin(pa_ctx *ctx, const double *betas, int32_t K, int32_t R, int3
                     uint64_t seed, const pa_anneal_opts *opts);
 
 /* Enqueue temperature steps [steps done, k_end) on the context's stream and
- * return without waiting (pa_sync waits). k_end is clamped to K. In adaptive
- * mode the steps after beta_max is reached are skipped on the device.
+ * return without waiting for them (pa_sync waits). k_end is clamped to K.
+ * In adaptive mode the steps after beta_max is reached are no-ops on the
+ * device; so that they are not enqueued by the thousand, an adaptive run is
+ * enqueued in chunks of 32 steps and the call waits (host side) until the
+ * device is at most four chunks behind, reading whether the run has ended; it
+ * then returns with the remaining steps counted as done. Not while the
+ * stream is being captured (there every step is enqueued, without waits).
  * Errors: PA_ESTATE (no pa_anneal_begin), PA_EINVAL, PA_ECUDA. */
 int pa_anneal_run(pa_ctx *ctx, int32_t k_end);
 
