@@ -47,6 +47,20 @@ def shape_key(g, R, S) -> str:
     return f"n{g.n}_m{g.m}_d{g.maxdeg}_w{int(g.w is not None)}_R{R}_S{S}"
 
 
+def candidates_for(g, context="alone", candidates=None):
+    """The candidates a graph admits in a context. "saturated" drops the
+    CTA-pair kernel, which only gains by balancing one instance over the SMs
+    (when other work fills the GPU that balance comes for free and its
+    cluster barriers are pure cost), and for the same reason runs the
+    multi-spin-coded layout with every word in one-CTA blocks (msc_no_split),
+    which a timing of the instance alone cannot show."""
+    cands = [c for c in (candidates or CANDIDATES) if feasible(g, c)]
+    if context != "alone":
+        cands = [c for c in cands if c.get("variant") != 3] or cands
+        cands = [dict(c, msc_no_split=1) if c.get("variant") == 1 else c for c in cands]
+    return cands
+
+
 def tune(g, betas, R, S, seed=0, steps=2, cache_path=None, candidates=None, context="alone"):
     """Return (best option dict, {candidate index: ms per million attempts}).
 
@@ -63,15 +77,7 @@ def tune(g, betas, R, S, seed=0, steps=2, cache_path=None, candidates=None, cont
             cache = json.load(f)
         if key in cache:
             return cache[key]["opts"], cache[key]["times"]
-    cands = [c for c in (candidates or CANDIDATES) if feasible(g, c)]
-    if context != "alone":
-        # The CTA-pair kernel only gains by balancing one instance over the SMs;
-        # when other work fills the GPU that balance comes for free and its
-        # cluster barriers are pure cost. For the same reason the multi-spin-
-        # coded layout runs every word in one-CTA blocks (msc_no_split), which
-        # a timing of the instance alone cannot show.
-        cands = [c for c in cands if c.get("variant") != 3] or cands
-        cands = [dict(c, msc_no_split=1) if c.get("variant") == 1 else c for c in cands]
+    cands = candidates_for(g, context, candidates)
     mid = max(0, len(betas) // 2 - steps)
     sl = list(betas[mid:mid + steps + 1])
     times = {}

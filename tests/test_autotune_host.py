@@ -32,3 +32,16 @@ def test_shape_key_and_cache_hit(tmp_path):
     opts, times = autotune.tune(g, wl.linear_betas(0.1, 1.0, 8), 4096, 4, cache_path=str(cache),
                                 context="saturated")
     assert opts == {"variant": 1} and times == {"0": 1.5}
+
+
+def test_saturated_context_drops_pairs_and_splits():
+    """Saturated: no CTA-pair kernel, and the one-CTA multi-spin-coded layout
+    runs every word in one kernel (msc_no_split); alone: the candidates as
+    listed."""
+    g = wl.gnp(60, 0.1, seed=1)
+    alone = autotune.candidates_for(g, "alone")
+    sat = autotune.candidates_for(g, "saturated")
+    assert alone == [c for c in autotune.CANDIDATES if autotune.feasible(g, c)]
+    assert all(c.get("variant") != 3 for c in sat)
+    assert [c for c in sat if c.get("variant") == 1] == [dict(variant=1, msc_no_split=1)]
+    assert [c for c in sat if c.get("variant") == 0] == [c for c in alone if c.get("variant") == 0]
